@@ -1,0 +1,388 @@
+"""Plain CPU oracle of Wally's BFV server evaluation (arXiv 2406.06761).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` are the only users.  The product
+library never imports this package, and this package never imports the
+product library.  The arithmetic lives in ``wally_oracle.c`` (compiled with
+gcc on first use); this wrapper adds the big-integer half of decryption
+(CRT composition and the t/Q scaling, Sec. 2 decryption formula), which Python
+integers state directly.
+
+Every function cites the passage of the paper it follows; the readings taken
+where the paper is silent are listed in the header of ``wally_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import functools
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wally_oracle.c")
+_BUILD = os.path.join(_HERE, "_oracle_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_MAX_MODS = 18
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, position independent, pthreads)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("logN", ctypes.c_uint32), ("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("d", ctypes.c_uint32),
+        ("d_pad", ctypes.c_uint32), ("g", ctypes.c_uint32), ("h", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("mod", ctypes.c_uint64 * _MAX_MODS), ("psi", ctypes.c_uint64 * _MAX_MODS),
+        ("delta", ctypes.c_uint64 * _MAX_MODS), ("k1", ctypes.c_uint64), ("kg", ctypes.c_uint64),
+    ]
+
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i8p = ctypes.POINTER(ctypes.c_int8)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_pp = ctypes.POINTER(_Params)
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            sig = {
+                "or_params_init": (ctypes.c_int, [ctypes.c_uint32] * 5 + [_u64p, ctypes.c_uint64, ctypes.c_uint64, _pp]),
+                "or_is_prime": (ctypes.c_int, [ctypes.c_uint64]),
+                "or_prev_prime_1mod": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
+                "or_smallest_root": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint32]),
+                "or_ntt_fwd": (None, [_pp, ctypes.c_uint32, _u64p]),
+                "or_ntt_inv": (None, [_pp, ctypes.c_uint32, _u64p]),
+                "or_polymul": (None, [_pp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
+                "or_polymul_schoolbook": (None, [_pp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
+                "or_automorphism": (None, [_pp, ctypes.c_uint32, ctypes.c_uint64, _u64p, _u64p]),
+                "or_slots_encode": (None, [_pp, _u64p, _u64p]),
+                "or_slots_decode": (None, [_pp, _u64p, _u64p]),
+                "or_replicate_query": (None, [_pp, _i32p, _u64p]),
+                "or_encode_cluster": (ctypes.c_int, [_pp, ctypes.c_uint32, _i8p, _u64p]),
+                "or_keygen": (None, [_pp, _i8p, ctypes.c_uint64, _u64p, _i8p, _u64p]),
+                "or_encrypt": (None, [_pp, _i8p, _u64p, _u64p, _i8p, _u64p]),
+                "or_decrypt_residues": (None, [_pp, _i8p, _u64p, _u64p]),
+                "or_rotate": (None, [_pp, ctypes.c_uint64, _u64p, _u64p, _u64p]),
+                "or_ptct_sum": (None, [_pp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
+                "or_ptxt_to_ntt": (None, [_pp, ctypes.c_uint32, _u64p, _u64p]),
+                "or_eval": (ctypes.c_int, [_pp, ctypes.c_uint32, _u64p, _u64p, _u64p, _u64p]),
+                "or_eval_batch": (ctypes.c_int, [_pp, ctypes.c_uint32, _u32p, ctypes.POINTER(_u64p), ctypes.c_uint32,
+                                                 _u32p, _u64p, _u64p, _u64p, _u64p, ctypes.c_uint32]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray, ty):
+    return a.ctypes.data_as(ty)
+
+
+def _u64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+def _i8(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int8)
+
+
+class Params:
+    """BFV/RNS parameters (Sec. 2, Sec. 7 "Parameters Selection").
+
+    ``mods[:L]`` are the ciphertext primes q_i, ``mods[L]`` the special prime P,
+    ``mods[L+1]`` the plaintext modulus t; modulus index j selects one of them
+    in the ring functions below.
+    """
+
+    def __init__(self, raw: _Params):
+        self.raw = raw
+        self.N = raw.N
+        self.log_n = raw.logN
+        self.L = raw.L
+        self.q = [int(raw.mod[i]) for i in range(raw.L)]
+        self.P = int(raw.mod[raw.L])
+        self.t = int(raw.mod[raw.L + 1])
+        self.mods = self.q + [self.P, self.t]
+        self.psi = [int(raw.psi[i]) for i in range(raw.L + 2)]
+        self.zeta_t = self.psi[raw.L + 1]
+        self.delta = [int(raw.delta[i]) for i in range(raw.L)]
+        self.d, self.d_pad, self.g, self.h = raw.d, raw.d_pad, raw.g, raw.h
+        self.k1, self.kg = int(raw.k1), int(raw.kg)
+        self.Q = 1
+        for q in self.q:
+            self.Q *= q
+
+    @property
+    def ptr(self):
+        return ctypes.byref(self.raw)
+
+
+@functools.lru_cache(maxsize=None)
+def params(log_n: int, L: int, q_bits: int, t_bits: int, dim: int,
+           q: tuple | None = None, p: int = 0, t: int = 0) -> Params:
+    """Derive the parameter set (primes by trial division, roots by search)."""
+    lib = _load()
+    raw = _Params()
+    qa = _u64(q) if q else None
+    rc = lib.or_params_init(log_n, L, q_bits, t_bits, dim, _p(qa, _u64p) if qa is not None else None, p, t,
+                            ctypes.byref(raw))
+    if rc != 0:
+        raise ValueError(f"or_params_init failed ({rc})")
+    return Params(raw)
+
+
+def is_prime(n: int) -> bool:
+    return bool(_load().or_is_prime(n))
+
+
+def prev_prime_1mod(below: int, step: int) -> int:
+    return int(_load().or_prev_prime_1mod(below, step))
+
+
+def smallest_root(t: int, n: int) -> int:
+    return int(_load().or_smallest_root(t, n))
+
+
+# ------------------------------------------------------------------ ring
+
+def ntt_fwd(prm: Params, j: int, a) -> np.ndarray:
+    """Negacyclic NTT: A[i] = sum_k a[k] psi^((2i+1)k) mod mods[j] (Sec. 7)."""
+    x = _u64(a).copy()
+    _load().or_ntt_fwd(prm.ptr, j, _p(x, _u64p))
+    return x
+
+
+def ntt_inv(prm: Params, j: int, a) -> np.ndarray:
+    x = _u64(a).copy()
+    _load().or_ntt_inv(prm.ptr, j, _p(x, _u64p))
+    return x
+
+
+def polymul(prm: Params, j: int, a, b) -> np.ndarray:
+    a, b = _u64(a), _u64(b)
+    out = np.empty(prm.N, np.uint64)
+    _load().or_polymul(prm.ptr, j, _p(a, _u64p), _p(b, _u64p), _p(out, _u64p))
+    return out
+
+
+def polymul_schoolbook(prm: Params, j: int, a, b) -> np.ndarray:
+    a, b = _u64(a), _u64(b)
+    out = np.empty(prm.N, np.uint64)
+    _load().or_polymul_schoolbook(prm.ptr, j, _p(a, _u64p), _p(b, _u64p), _p(out, _u64p))
+    return out
+
+
+def automorphism(prm: Params, j: int, k: int, a) -> np.ndarray:
+    """sigma_k : a(X) -> a(X^k) mod (X^N+1, mods[j]) (Sec. 2 CtRotate, Sec. 4.2)."""
+    a = _u64(a)
+    out = np.empty(prm.N, np.uint64)
+    _load().or_automorphism(prm.ptr, j, k, _p(a, _u64p), _p(out, _u64p))
+    return out
+
+
+def galois_element(prm: Params, r: int) -> int:
+    """Left row rotation by r is sigma_(3^r mod 2N) (Sec. 2 CtRotate)."""
+    return pow(3, r, 2 * prm.N)
+
+
+# ------------------------------------------------------------------ slots
+
+def slots_encode(prm: Params, v) -> np.ndarray:
+    """Slot vector (values mod t, linear index rho*N/2 + c) -> polynomial mod t."""
+    v = _u64(v)
+    out = np.empty(prm.N, np.uint64)
+    _load().or_slots_encode(prm.ptr, _p(v, _u64p), _p(out, _u64p))
+    return out
+
+
+def slots_decode(prm: Params, m) -> np.ndarray:
+    m = _u64(m)
+    out = np.empty(prm.N, np.uint64)
+    _load().or_slots_decode(prm.ptr, _p(m, _u64p), _p(out, _u64p))
+    return out
+
+
+def replicate_query(prm: Params, q) -> np.ndarray:
+    """Alg. "Client Query Generation": the query repeated n/d_pad times (zeros for a fake)."""
+    out = np.empty(prm.N, np.uint64)
+    if q is None:
+        _load().or_replicate_query(prm.ptr, None, _p(out, _u64p))
+    else:
+        qa = np.ascontiguousarray(q, dtype=np.int32)
+        _load().or_replicate_query(prm.ptr, _p(qa, _i32p), _p(out, _u64p))
+    return out
+
+
+def encode_cluster(prm: Params, emb) -> tuple[int, np.ndarray]:
+    """Alg. "Server Initialization": diagonals, packing, BSGS pre-rotation, encoding.
+
+    Returns (m, plaintexts[m][h][g][L][N]) in coefficient form."""
+    emb = _i8(emb).reshape(-1, prm.d) if len(emb) else np.zeros((0, prm.d), np.int8)
+    size = emb.shape[0]
+    m = max(1, -(-size // prm.N))
+    out = np.empty((m, prm.h, prm.g, prm.L, prm.N), np.uint64)
+    got = _load().or_encode_cluster(prm.ptr, size, _p(emb, _i8p) if size else None, _p(out, _u64p))
+    assert got == m
+    return m, out
+
+
+# ------------------------------------------------------------------ client
+
+def keygen(prm: Params, s, k: int, a_rand, e_rand) -> np.ndarray:
+    """Galois key for element k, layout [L][2][L+1][N] (Sec. 5, Sec. 7 hybrid key switching)."""
+    s, a_rand, e_rand = _i8(s), _u64(a_rand), _i8(e_rand)
+    assert a_rand.size == prm.L * (prm.L + 1) * prm.N and e_rand.size == prm.L * prm.N
+    out = np.empty((prm.L, 2, prm.L + 1, prm.N), np.uint64)
+    _load().or_keygen(prm.ptr, _p(s, _i8p), k, _p(a_rand, _u64p), _p(e_rand, _i8p), _p(out, _u64p))
+    return out
+
+
+def keygen_pair(prm: Params, s, a_rand, e_rand) -> np.ndarray:
+    """The two keys a query carries (Sec. 7 "Reducing the request size"): rotation by 1, by g."""
+    a_rand = _u64(a_rand).reshape(2, -1)
+    e_rand = _i8(e_rand).reshape(2, -1)
+    return np.stack([keygen(prm, s, prm.k1, a_rand[0], e_rand[0]), keygen(prm, s, prm.kg, a_rand[1], e_rand[1])])
+
+
+def encrypt(prm: Params, s, m_poly, a_rand, e) -> np.ndarray:
+    """Symmetric BFV encryption of a plaintext polynomial m (coefficients in [0, t))."""
+    s, m_poly, a_rand, e = _i8(s), _u64(m_poly), _u64(a_rand), _i8(e)
+    out = np.empty((2, prm.L, prm.N), np.uint64)
+    _load().or_encrypt(prm.ptr, _p(s, _i8p), _p(m_poly, _u64p), _p(a_rand, _u64p), _p(e, _i8p), _p(out, _u64p))
+    return out
+
+
+def encrypt_slots(prm: Params, s, v, a_rand, e) -> np.ndarray:
+    return encrypt(prm, s, slots_encode(prm, v), a_rand, e)
+
+
+def encrypt_query(prm: Params, s, q, a_rand, e) -> np.ndarray:
+    """EncSemPt of the replicated query (Alg. "Client Query Generation"); q=None is a fake."""
+    return encrypt_slots(prm, s, replicate_query(prm, q), a_rand, e)
+
+
+def _crt(prm: Params, x: np.ndarray) -> list[int]:
+    Q = prm.Q
+    coef = []
+    for qi in prm.q:
+        Qi = Q // qi
+        coef.append(Qi * pow(Qi % qi, -1, qi))
+    rows = [[int(v) for v in x[i]] for i in range(prm.L)]
+    return [sum(rows[i][n] * coef[i] for i in range(prm.L)) % Q for n in range(prm.N)]
+
+
+def decrypt_poly(prm: Params, s, ct) -> tuple[np.ndarray, list[int]]:
+    """Sec. 2 decryption: x = [c0 + c1*s]_Q, m = round(t*x/Q) mod t (ties up).
+
+    Returns (m coefficients, x as Python integers)."""
+    s, ct = _i8(s), _u64(ct)
+    x = np.empty((prm.L, prm.N), np.uint64)
+    _load().or_decrypt_residues(prm.ptr, _p(s, _i8p), _p(ct, _u64p), _p(x, _u64p))
+    xs = _crt(prm, x)
+    Q, t = prm.Q, prm.t
+    m = np.array([((t * v + Q // 2) // Q) % t for v in xs], dtype=np.uint64)
+    return m, xs
+
+
+def decrypt_slots(prm: Params, s, ct) -> np.ndarray:
+    """Decrypt and decode; slot values centred into (-t/2, t/2]."""
+    m, _ = decrypt_poly(prm, s, ct)
+    v = slots_decode(prm, m).astype(np.int64)
+    t = prm.t
+    return np.where(v > t // 2, v - t, v)
+
+
+def noise_bits(prm: Params, s, ct) -> float:
+    """log2 of the infinity norm of e = [c0 + c1*s - Delta*m]_Q (centred)."""
+    m, xs = decrypt_poly(prm, s, ct)
+    Q = prm.Q
+    delta = Q // prm.t
+    worst = 0
+    for v, mv in zip(xs, m):
+        e = (v - delta * int(mv)) % Q
+        if e > Q // 2:
+            e = Q - e
+        worst = max(worst, e)
+    return float(np.log2(worst)) if worst else 0.0
+
+
+def noise_budget_bits(prm: Params, s, ct) -> float:
+    """log2(Q/2t) - log2||e||: decryption is correct while this is positive (Sec. 2)."""
+    return float(np.log2(prm.Q / (2 * prm.t))) - noise_bits(prm, s, ct)
+
+
+# ------------------------------------------------------------------ server
+
+def rotate(prm: Params, k: int, key, ct) -> np.ndarray:
+    """Rot_k = automorphism + hybrid key switching, key [L][2][L+1][N] coefficient form."""
+    key, ct = _u64(key), _u64(ct)
+    out = np.empty((2, prm.L, prm.N), np.uint64)
+    _load().or_rotate(prm.ptr, k, _p(key, _u64p), _p(ct, _u64p), _p(out, _u64p))
+    return out
+
+
+def ptct_sum(prm: Params, ptxt, cts) -> np.ndarray:
+    """sum_b P_b * ct_b (PtCtMult + CtCtAdd, Sec. 2)."""
+    ptxt, cts = _u64(ptxt), _u64(cts)
+    count = ptxt.size // (prm.L * prm.N)
+    out = np.empty((2, prm.L, prm.N), np.uint64)
+    _load().or_ptct_sum(prm.ptr, count, _p(ptxt, _u64p), _p(cts, _u64p), _p(out, _u64p))
+    return out
+
+
+def ptxt_to_ntt(prm: Params, m: int, ptxt) -> np.ndarray:
+    ptxt = _u64(ptxt)
+    out = np.empty_like(ptxt)
+    _load().or_ptxt_to_ntt(prm.ptr, m, _p(ptxt, _u64p), _p(out, _u64p))
+    return out
+
+
+def eval_query(prm: Params, m: int, ptxt, ct, keys) -> np.ndarray:
+    """Alg. "Server Computation" for one query; returns [m][2][L][N] coefficient form."""
+    ptxt, ct, keys = _u64(ptxt), _u64(ct), _u64(keys)
+    out = np.empty((m, 2, prm.L, prm.N), np.uint64)
+    rc = _load().or_eval(prm.ptr, m, _p(ptxt, _u64p), _p(ct, _u64p), _p(keys, _u64p), _p(out, _u64p))
+    if rc != 0:
+        raise ValueError("or_eval rejected the input (chunks must satisfy 0 < m < g)")
+    return out
+
+
+def eval_batch(prm: Params, clusters_ntt: list, ids, cts, keys, nthreads: int | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """Many queries; clusters_ntt[c] = (m_c, plaintexts of cluster c in NTT form).
+
+    Returns (out [sum m][2][L][N], chunk offsets [nq])."""
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    cts, keys = _u64(cts), _u64(keys)
+    chunks = np.array([c[0] for c in clusters_ntt], dtype=np.uint32)
+    arrs = [_u64(c[1]) for c in clusters_ntt]
+    ptrs = (_u64p * len(arrs))(*[_p(a, _u64p) for a in arrs])
+    offs = np.zeros(len(ids), dtype=np.uint64)
+    if len(ids):
+        offs[1:] = np.cumsum(chunks[ids])[:-1]
+    total = int(chunks[ids].sum()) if len(ids) else 0
+    out = np.empty((total, 2, prm.L, prm.N), np.uint64)
+    rc = _load().or_eval_batch(prm.ptr, len(arrs), _p(chunks, _u32p), ptrs, len(ids), _p(ids, _u32p),
+                               _p(cts, _u64p), _p(keys, _u64p), _p(offs, _u64p), _p(out, _u64p),
+                               nthreads or os.cpu_count() or 1)
+    if rc != 0:
+        raise ValueError("or_eval_batch rejected the input")
+    return out, offs

@@ -1,0 +1,411 @@
+"""Pins of the CPU oracle against the mathematics and the paper (no GPU).
+
+Each test checks the oracle against something other than itself: a library
+routine (sympy primality, numpy convolution), a closed form, direct
+evaluation, a big-integer restatement (tests/bigint_ref.py), a worked example
+printed in the paper (tests/golden/), or decryption of the result.
+"""
+import os
+
+import numpy as np
+import pytest
+import sympy
+
+import oracle as O
+from paper_2406_06761_gb300 import workload as W
+from tests import bigint_ref as B
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(i=0):
+    return np.random.default_rng(1234 + i)
+
+
+def _rand_poly(p, N, i=0):
+    return _rng(i).integers(0, p, size=N, dtype=np.uint64)
+
+
+# ------------------------------------------------------------------ parameters
+
+@pytest.mark.parametrize("name", ["tiny", "batched", "wide"])
+def test_primes_are_the_largest_of_their_form(name):
+    """Sec. 2 "Vectorized SHE" (t prime, t = 1 mod 2n) and the configs' rule for
+    q_i: the largest primes = 1 mod 2N below 2^bits; P the next one below."""
+    w = W.WORKLOADS[name]
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    two_n = 2 * prm.N
+    bound = 1 << w.q_bits
+    for x in prm.q + [prm.P]:
+        assert sympy.isprime(x) and x % two_n == 1
+    chain = [bound] + prm.q + [prm.P]
+    for hi, lo in zip(chain, chain[1:]):
+        # no prime of the form strictly between lo and hi
+        c = lo + two_n
+        while c < hi:
+            assert not sympy.isprime(c)
+            c += two_n
+    t = prm.t
+    assert sympy.isprime(t) and t % two_n == 1 and t < (1 << w.t_bits)
+    c = t + two_n
+    while c < (1 << w.t_bits):
+        assert not sympy.isprime(c)
+        c += two_n
+
+
+@pytest.mark.parametrize("name", ["tiny", "batched", "wide"])
+def test_delta_is_floor_q_over_t(name):
+    """Sec. 2: ciphertexts carry floor(Q/t)*m; the oracle stores it per limb."""
+    w = W.WORKLOADS[name]
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    delta = prm.Q // prm.t
+    assert prm.delta == [delta % q for q in prm.q]
+
+
+@pytest.mark.parametrize("name", ["tiny", "batched", "wide"])
+def test_slot_root_is_smallest_primitive_2n_root(name):
+    """Reading R7: zeta_t is the smallest x of multiplicative order 2N mod t."""
+    w = W.WORKLOADS[name]
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    z = prm.zeta_t
+    assert sympy.n_order(z, prm.t) == 2 * prm.N
+    for x in range(2, z):
+        assert sympy.n_order(x, prm.t) != 2 * prm.N
+
+
+def test_bsgs_dimensions_match_paper():
+    """Sec. 4.1 packing / BSGS counts (tests/golden/packing_sec41.txt)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "packing_sec41.txt")) if l.strip() and l[0] != "#"]
+    for n, nprime, d_pad, mults, resp, g, h in (map(int, r) for r in rows):
+        log_n = n.bit_length() - 1
+        prm = O.params(log_n, 1, 40 if log_n < 14 else 50, 22 if log_n == 14 else 20, d_pad)
+        m = -(-nprime // n)
+        assert prm.d_pad == d_pad and prm.g == g and prm.h == h
+        assert m * prm.g * prm.h == mults and m == resp
+
+
+# ------------------------------------------------------------------ NTT / ring
+
+def test_ntt_is_evaluation_at_odd_powers(small_params):
+    """A[i] = a(psi^(2i+1)): direct evaluation with Python integers."""
+    prm = small_params
+    for j in range(prm.L + 2):
+        p, psi = prm.mods[j], prm.psi[j]
+        assert pow(psi, prm.N, p) == p - 1
+        a = _rand_poly(p, prm.N, j)
+        A = O.ntt_fwd(prm, j, a)
+        for i in range(prm.N):
+            x = pow(psi, 2 * i + 1, p)
+            assert int(A[i]) == sum(int(a[k]) * pow(x, k, p) for k in range(prm.N)) % p
+        assert np.array_equal(O.ntt_inv(prm, j, A), a)
+
+
+def test_polymul_matches_numpy_convolution(small_params):
+    """Negacyclic product = linear convolution folded by X^N = -1."""
+    prm = small_params
+    for j in range(prm.L + 1):
+        p = prm.mods[j]
+        a, b = _rand_poly(p, prm.N, 10 + j), _rand_poly(p, prm.N, 20 + j)
+        full = np.convolve(a.astype(object), b.astype(object))
+        ref = [(int(full[k]) - (int(full[k + prm.N]) if k + prm.N < len(full) else 0)) % p for k in range(prm.N)]
+        assert [int(v) for v in O.polymul(prm, j, a, b)] == ref
+        assert [int(v) for v in O.polymul_schoolbook(prm, j, a, b)] == ref
+
+
+def test_polymul_spot_check_n4096(tiny_params):
+    """At N = 4096, sampled coefficients of the NTT product by direct sums."""
+    prm = tiny_params
+    p = prm.q[0]
+    a, b = _rand_poly(p, prm.N, 3), _rand_poly(p, prm.N, 4)
+    c = O.polymul(prm, 0, a, b)
+    ai, bi = [int(v) for v in a], [int(v) for v in b]
+    N = prm.N
+    for k in (0, 1, 17, 2048, 4095):
+        s = sum(ai[x] * bi[k - x] for x in range(k + 1)) - sum(ai[x] * bi[k + N - x] for x in range(k + 1, N))
+        assert int(c[k]) == s % p
+
+
+def test_galois_worked_example():
+    """Sec. 4.2: g_a = n/2^a + 1, and 129^2 = 257 (mod 8192) (golden file)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "galois_sec42.txt")) if l.strip() and l[0] != "#"]
+    prm = O.params(12, 1, 36, 17, 192)
+    for r in rows:
+        if r[0] == "square":
+            n, base, res = int(r[1]), int(r[2]), int(r[3])
+            assert n == prm.N
+            a = _rand_poly(prm.q[0], prm.N, 7)
+            twice = O.automorphism(prm, 0, base, O.automorphism(prm, 0, base, a))
+            assert np.array_equal(twice, O.automorphism(prm, 0, res, a))
+        else:
+            n, a_idx, ga = map(int, r)
+            assert n // 2 ** a_idx + 1 == ga
+
+
+def test_automorphism_composition_and_evaluation(small_params):
+    """sigma_a o sigma_b = sigma_(ab mod 2N); (sigma_k a)(x) = a(x^k) at the roots."""
+    prm = small_params
+    p, psi, N = prm.q[0], prm.psi[0], prm.N
+    a = _rand_poly(p, N, 5)
+    for ka, kb in [(3, 5), (3, 3), (7, 2 * N - 1), (prm.kg, prm.k1)]:
+        lhs = O.automorphism(prm, 0, ka, O.automorphism(prm, 0, kb, a))
+        assert np.array_equal(lhs, O.automorphism(prm, 0, (ka * kb) % (2 * N), a))
+    for k in (3, prm.kg):
+        sa = O.automorphism(prm, 0, k, a)
+        for i in range(N):
+            x = pow(psi, 2 * i + 1, p)
+            lhs = sum(int(sa[n]) * pow(x, n, p) for n in range(N)) % p
+            rhs = sum(int(a[n]) * pow(x, n * k, p) for n in range(N)) % p
+            assert lhs == rhs
+
+
+# ------------------------------------------------------------------ slots
+
+def _rowrot(v, r, N):
+    h = N // 2
+    return np.concatenate([np.roll(v[:h], -r), np.roll(v[h:], -r)])
+
+
+def test_slot_encoding_is_evaluation(small_params):
+    """Reading R7: slot (rho, c) = m(zeta^(+-3^c)); encode is its inverse."""
+    prm = small_params
+    N, t, z = prm.N, prm.t, prm.zeta_t
+    v = _rng(8).integers(0, t, size=N, dtype=np.uint64)
+    m = O.slots_encode(prm, v)
+    for s in range(N):
+        rho, c = divmod(s, N // 2)
+        e = pow(3, c, 2 * N)
+        if rho:
+            e = 2 * N - e
+        x = pow(z, e, t)
+        assert sum(int(m[k]) * pow(x, k, t) for k in range(N)) % t == int(v[s])
+    assert np.array_equal(O.slots_decode(prm, m), v)
+
+
+@pytest.mark.parametrize("which", ["small", "tiny"])
+def test_rotation_is_left_row_shift(which, small_params, tiny_params):
+    """Sec. 2 CtRotate: sigma_(3^r) shifts both rows left by r (reading R6)."""
+    prm = small_params if which == "small" else tiny_params
+    N, t = prm.N, prm.t
+    v = _rng(9).integers(0, t, size=N, dtype=np.uint64)
+    m = O.slots_encode(prm, v)
+    jt = prm.L + 1
+    for r in (1, 2, prm.g, N // 2 - 1):
+        k = O.galois_element(prm, r)
+        got = O.slots_decode(prm, O.automorphism(prm, jt, k, m))
+        assert np.array_equal(got, _rowrot(v, r, N))
+
+
+def test_replicate_query_layout(tiny_params):
+    """Alg. "Client Query Generation": n/d_pad copies of q, zero padding."""
+    prm = tiny_params
+    q = _rng(11).integers(-15, 16, size=prm.d)
+    v = O.replicate_query(prm, q).astype(np.int64)
+    v = np.where(v > prm.t // 2, v - prm.t, v)
+    blocks = v.reshape(-1, prm.d_pad)
+    assert np.all(blocks[:, :prm.d] == q) and np.all(blocks[:, prm.d:] == 0)
+    assert np.all(O.replicate_query(prm, None) == 0)
+
+
+def _decode_plaintexts(prm, pt):
+    """Decode every P' of a cluster back to slot values, centred."""
+    t = prm.t
+    out = np.empty(pt.shape[:3] + (prm.N,), dtype=np.int64)
+    for idx in np.ndindex(*pt.shape[:3]):
+        lim = pt[idx][0].astype(object)
+        q0 = prm.q[0]
+        cen = [int(x) - q0 if int(x) > q0 // 2 else int(x) for x in lim]
+        mt = np.array([c % t for c in cen], dtype=np.uint64)
+        v = O.slots_decode(prm, mt).astype(np.int64)
+        out[idx] = np.where(v > t // 2, v - t, v)
+    return out
+
+
+def test_cluster_encoding_bsgs_identity(tiny_params):
+    """Sec. 4.1 diagonal identity with BSGS (Alg. "Server Initialization",
+    Alg. "Server Computation"): in the slot domain,
+    sum_i rowrot(sum_b P'_{i,b} * rowrot(q, b), g*i) = E q for every slot."""
+    prm = tiny_params
+    N, g, h = prm.N, prm.g, prm.h
+    E = W.embeddings(700, prm.d, 15, seed=5)
+    q = W.query_vectors(1, prm.d, 15, seed=5)[0]
+    m, pt = O.encode_cluster(prm, E)
+    assert m == 1
+    dec = _decode_plaintexts(prm, pt)
+    qrep = O.replicate_query(prm, q).astype(np.int64)
+    qrep = np.where(qrep > prm.t // 2, qrep - prm.t, qrep)
+    total = np.zeros(N, dtype=np.int64)
+    for i in range(h):
+        Ti = sum(dec[0, i, b] * _rowrot(qrep, b, N) for b in range(g))
+        total += _rowrot(Ti, g * i, N)
+    expect = np.zeros(N, dtype=np.int64)
+    expect[:700] = E.astype(np.int64) @ q.astype(np.int64)
+    assert np.array_equal(total, expect)
+    # same as the plain diagonal method of Sec. 4.1 (d rotations, no BSGS)
+    plain = np.zeros(N, dtype=np.int64)
+    for i in range(h):
+        for b in range(g):
+            pj = _rowrot(dec[0, i, b], g * i, N)   # undo the pre-rotation by -g*i
+            plain += pj * _rowrot(qrep, g * i + b, N)
+    assert np.array_equal(plain, expect)
+
+
+def test_cluster_encoding_two_chunks_and_padding():
+    """m = ceil(|C|/N) chunks; padding of d and of the last chunk is zero."""
+    prm = O.params(12, 1, 36, 17, 100)   # d = 100 -> d_pad = 128, g = 16, h = 8
+    assert (prm.d_pad, prm.g, prm.h) == (128, 16, 8)
+    E = W.embeddings(prm.N + 5, prm.d, 15, seed=6)
+    m, pt = O.encode_cluster(prm, E)
+    assert m == 2
+    dec = _decode_plaintexts(prm, pt)
+    # chunk 1, diagonal j = 0 (i = 0, b = 0): slots s < 5 hold E[N+s][s mod 128]
+    d0 = dec[1, 0, 0]
+    for s in range(5):
+        assert d0[s] == E[prm.N + s][s % prm.d_pad]
+    assert np.all(d0[5:] == 0)
+    # diagonal 1 at slot x = 127 reads column 0 of embedding 127 (wrap-around)
+    assert dec[0, 0, 1][127] == E[127][0]
+    # column x + j >= d is padding
+    assert dec[0, 0, 1][99] == 0
+
+
+# ------------------------------------------------------------------ client
+
+def test_encrypt_decrypt_roundtrip(tiny_params):
+    prm = tiny_params
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P, seed=3)
+    v = _rng(12).integers(0, prm.t, size=prm.N, dtype=np.uint64)
+    ct = O.encrypt_slots(prm, cr.secret[0], v, cr.enc_a[0], cr.enc_e[0])
+    got = O.decrypt_slots(prm, cr.secret[0], ct)
+    vc = v.astype(np.int64)
+    assert np.array_equal(got, np.where(vc > prm.t // 2, vc - prm.t, vc))
+    # fresh noise is exactly the drawn error: ||e|| <= 19
+    assert O.noise_bits(prm, cr.secret[0], ct) <= np.log2(19) + 1e-9
+
+
+def test_galois_key_relation(small_params):
+    """Reading R2/R3: b_i + a_i*s = e_i + [i=j] P sigma_k(s) on every modulus."""
+    prm = small_params
+    N, L, P = prm.N, prm.L, prm.P
+    cr = W.client_randomness(1, N, prm.q, P, seed=4)
+    s = cr.secret[0].astype(np.int64)
+    key = O.keygen(prm, cr.secret[0], prm.kg, cr.key_a[0, 1], cr.key_e[0, 1])
+    sk = B.automorphism([int(x) for x in s], prm.kg, 1 << 200)
+    sk = [x - (1 << 200) if x > (1 << 199) else x for x in sk]
+    for i in range(L):
+        e = cr.key_e[0, 1, i].astype(np.int64)
+        for j, p in enumerate(prm.q + [P]):
+            b, a = key[i, 0, j], key[i, 1, j]
+            lhs = [(int(x) + y) % p for x, y in zip(b, B.negacyclic_mul(a, [int(v) % p for v in s], p))]
+            rhs = [(int(e[n]) + (P * sk[n] if i == j else 0)) % p for n in range(N)]
+            assert lhs == rhs
+
+
+# ------------------------------------------------------------------ server
+
+def test_rotation_bits_match_bigint_definition(small_params):
+    """Hybrid key switching (Sec. 7), readings R3/R4: the RNS result equals
+    round(sum_i d_i key_i / P) computed over Z_QP with big integers."""
+    prm = small_params
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P, seed=5)
+    keys = O.keygen_pair(prm, cr.secret[0], cr.key_a[0], cr.key_e[0])
+    v = _rng(13).integers(0, prm.t, size=prm.N, dtype=np.uint64)
+    ct = O.encrypt_slots(prm, cr.secret[0], v, cr.enc_a[0], cr.enc_e[0])
+    for which, k in ((0, prm.k1), (1, prm.kg)):
+        got = O.rotate(prm, k, keys[which], ct)
+        ref = B.rotate(prm, k, keys[which].tolist(), ct.tolist())
+        assert got.tolist() == ref
+
+
+@pytest.mark.parametrize("which", ["small", "tiny"])
+def test_rotation_decrypts_to_shift(which, small_params, tiny_params):
+    """Sec. 2 CtRotate semantics through encryption; noise stays small."""
+    prm = small_params if which == "small" else tiny_params
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P, seed=6)
+    keys = O.keygen_pair(prm, cr.secret[0], cr.key_a[0], cr.key_e[0])
+    v = _rng(14).integers(0, prm.t, size=prm.N, dtype=np.uint64)
+    ct = O.encrypt_slots(prm, cr.secret[0], v, cr.enc_a[0], cr.enc_e[0])
+    vc = v.astype(np.int64)
+    vc = np.where(vc > prm.t // 2, vc - prm.t, vc)
+    for which_key, r in ((0, 1), (1, prm.g)):
+        k = O.galois_element(prm, r)
+        out = O.rotate(prm, k, keys[which_key], ct)
+        assert np.array_equal(O.decrypt_slots(prm, cr.secret[0], out), _rowrot(vc, r, prm.N))
+        # key-switching noise: sum_i d_i e_i / P is about L * 19 * N in the worst case
+        assert O.noise_bits(prm, cr.secret[0], out) < np.log2(prm.L * 19 * prm.N) + 2
+
+
+def test_ptct_sum_matches_bigint(small_params):
+    prm = small_params
+    rng = _rng(15)
+    pts = [[rng.integers(0, q, size=prm.N, dtype=np.uint64) for q in prm.q] for _ in range(3)]
+    cts = [[[rng.integers(0, q, size=prm.N, dtype=np.uint64) for q in prm.q] for _ in range(2)] for _ in range(3)]
+    got = O.ptct_sum(prm, np.array(pts), np.array(cts))
+    ref = B.ptct_sum(prm, [[list(map(int, l)) for l in p] for p in pts],
+                     [[[list(map(int, l)) for l in c] for c in ct] for ct in cts])
+    assert got.tolist() == ref
+
+
+def test_eval_bits_match_bigint_small(small_params):
+    """Whole Alg. "Server Computation" at N = 16 (d = 4, g = h = 2), bit for bit."""
+    prm = small_params
+    assert (prm.g, prm.h) == (2, 2)
+    E = W.embeddings(11, prm.d, 15, seed=7)
+    q = W.query_vectors(1, prm.d, 15, seed=7)[0]
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P, seed=7)
+    keys = O.keygen_pair(prm, cr.secret[0], cr.key_a[0], cr.key_e[0])
+    ct = O.encrypt_query(prm, cr.secret[0], q, cr.enc_a[0], cr.enc_e[0])
+    m, pt = O.encode_cluster(prm, E)
+    got = O.eval_query(prm, m, pt, ct, keys)
+    ref = B.eval_query(prm, pt.tolist(), ct.tolist(), [keys[0].tolist(), keys[1].tolist()])
+    assert got.tolist() == ref
+    sc = O.decrypt_slots(prm, cr.secret[0], got[0])
+    assert np.array_equal(sc[:11], (E.astype(np.int64) @ q.astype(np.int64) + prm.t // 2) % prm.t - prm.t // 2)
+
+
+def test_eval_tiny_decrypts_to_scores(tiny_params):
+    """The tiny workload end to end: decrypt(eval(Enc(q))) = E q exactly
+    (|E q| <= 192 * 15^2 < t/2, so no wrap, Sec. 7 fixed-point condition),
+    padding slots decrypt to 0, and the noise budget stays positive."""
+    prm = tiny_params
+    w = W.WORKLOADS["tiny"]
+    sizes = W.cluster_sizes(w)
+    E = W.embeddings(int(sizes.sum()), w.dim, w.entry_bound)
+    q = W.query_vectors(1, w.dim, w.entry_bound)[0]
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P)
+    m, pt = O.encode_cluster(prm, E)
+    keys = O.keygen_pair(prm, cr.secret[0], cr.key_a[0], cr.key_e[0])
+    ct = O.encrypt_query(prm, cr.secret[0], q, cr.enc_a[0], cr.enc_e[0])
+    out = O.eval_query(prm, m, pt, ct, keys)
+    sc = O.decrypt_slots(prm, cr.secret[0], out[0])
+    assert np.array_equal(sc[:len(E)], E.astype(np.int64) @ q.astype(np.int64))
+    assert np.all(sc[len(E):] == 0)
+    assert O.noise_budget_bits(prm, cr.secret[0], out[0]) > 5
+    # a fake query (all-zero vector) scores zero everywhere
+    ctf = O.encrypt_query(prm, cr.secret[0], None, cr.enc_a[0], cr.enc_e[0])
+    assert np.all(O.decrypt_slots(prm, cr.secret[0], O.eval_query(prm, m, pt, ctf, keys)[0]) == 0)
+
+
+def test_eval_rejects_too_many_chunks(tiny_params):
+    """Sec. 5: BSGS is used only while the chunk count is below sqrt(d)."""
+    prm = tiny_params
+    with pytest.raises(ValueError):
+        O.eval_query(prm, prm.g, np.zeros((prm.g, prm.h, prm.g, prm.L, prm.N), np.uint64),
+                     np.zeros((2, prm.L, prm.N), np.uint64), np.zeros((2, prm.L, 2, prm.L + 1, prm.N), np.uint64))
+
+
+def test_eval_batch_equals_single(tiny_params):
+    """The threaded batch driver returns exactly the per-query results."""
+    prm = tiny_params
+    E1 = W.embeddings(300, prm.d, 15, seed=8)
+    E2 = W.embeddings(900, prm.d, 15, seed=9)
+    (m1, p1), (m2, p2) = O.encode_cluster(prm, E1), O.encode_cluster(prm, E2)
+    cr = W.client_randomness(3, prm.N, prm.q, prm.P, seed=8)
+    qs = W.query_vectors(3, prm.d, 15, seed=8)
+    keys = np.stack([O.keygen_pair(prm, cr.secret[i], cr.key_a[i], cr.key_e[i]) for i in range(3)])
+    cts = np.stack([O.encrypt_query(prm, cr.secret[i], qs[i], cr.enc_a[i], cr.enc_e[i]) for i in range(3)])
+    ids = np.array([1, 0, 1], np.uint32)
+    out, offs = O.eval_batch(prm, [(m1, O.ptxt_to_ntt(prm, m1, p1)), (m2, O.ptxt_to_ntt(prm, m2, p2))],
+                             ids, cts, keys, nthreads=3)
+    for i, c in enumerate(ids):
+        m, pt = (m1, p1) if c == 0 else (m2, p2)
+        assert np.array_equal(out[offs[i]:offs[i] + m], O.eval_query(prm, m, pt, cts[i], keys[i]))

@@ -1,0 +1,203 @@
+/*
+ * wally.h -- C ABI of the GB300 library for Wally's server-side encrypted
+ * similarity computation (arXiv 2406.06761, "Wally: Batched Private Nearest
+ * Neighbor Search at Scale").
+ *
+ * The server holds a database of embeddings split into clusters.  Each query
+ * is a BFV ciphertext of the client's embedding (replicated across the slots)
+ * plus two fresh Galois keys, and names one cluster.  The server returns, per
+ * chunk of that cluster, one ciphertext whose slots are the dot products of
+ * the query with every embedding of the chunk (Sec. 4.1, Sec. 5 "Server
+ * computation", Alg. "Server Computation").
+ *
+ * Conventions shared by every call:
+ *  - N ring degree, L ciphertext limbs q_0..q_{L-1}, P the special prime of
+ *    hybrid key switching (Sec. 7), t the plaintext modulus, d the embedding
+ *    dimension, d_pad = g*h its padding, g baby steps, h giant steps.
+ *  - Polynomials are N consecutive uint64_t residues in [0, modulus), in
+ *    COEFFICIENT form (coefficient of X^n at index n) at the boundary.
+ *  - ciphertext  : uint64_t [2][L][N]             (c0, c1 with c0 + c1*s = Delta*m + e)
+ *  - galois keys : uint64_t [2][L][2][L+1][N]     (key for left rotation by 1, then by g;
+ *                  per key: digit i < L, component (b, a), modulus q_0..q_{L-1}, P)
+ *  - "device" pointers are CUDA device memory of the context's device;
+ *    "host" pointers are ordinary host memory.  Pointers must be 16-byte
+ *    aligned.  The caller owns every buffer it passes; no call keeps a caller
+ *    pointer after it returns (asynchronous calls: after the stream reaches
+ *    the work, i.e. after wally_sync).
+ *  - Every call returns WALLY_OK or an error code; wally_last_error() gives a
+ *    thread-local message.  Nothing throws across the ABI.  Device-side
+ *    problems of asynchronous calls (a cluster id out of range) are recorded
+ *    in the context and reported by wally_sync.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).
+ */
+#ifndef WALLY_H
+#define WALLY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    WALLY_OK = 0,
+    WALLY_EINVAL = 1,   /* bad argument: shape, range, null pointer, unsupported size */
+    WALLY_ENOMEM = 2,   /* device or host allocation failed */
+    WALLY_ECUDA = 3,    /* a CUDA runtime call failed */
+    WALLY_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    WALLY_ESTATE = 5    /* call out of order (e.g. eval before load_clusters) */
+};
+
+#define WALLY_MAX_LIMBS 8
+
+typedef struct wally_ctx wally_ctx;
+
+/* Parameter request (Sec. 7 "Parameters Selection"; the configurations this
+ * library is measured on use N = 4096/8192/16384 and 36- or 50-bit limbs).
+ * q_i = the num_q largest primes = 1 mod 2N below 2^q_bits, P = the next such
+ * prime below q_{L-1}, t = the largest such prime below 2^t_bits, unless the
+ * explicit overrides are given. */
+typedef struct {
+    uint32_t log_n;        /* 12, 13 or 14 */
+    uint32_t num_q;        /* L, 1..WALLY_MAX_LIMBS-1 */
+    uint32_t q_bits;       /* bit size of the ciphertext primes, <= 61 */
+    uint32_t t_bits;       /* bit size of the plaintext prime, <= 30 */
+    uint32_t dim;          /* embedding dimension d; d_pad = next power of two */
+    int32_t device;        /* CUDA device ordinal */
+    const uint64_t *q;     /* optional [num_q] explicit primes, NULL = derive */
+    uint64_t p_special;    /* optional explicit P, 0 = derive */
+    uint64_t t;            /* optional explicit t, 0 = derive */
+    uint32_t max_wave;     /* queries per internal wave of wally_eval_batch, 0 = 1024 */
+} wally_params;
+
+typedef struct {
+    uint32_t n, log_n, num_q, dim, d_pad, g, h;
+    uint32_t num_clusters;           /* after wally_load_clusters */
+    uint64_t q[WALLY_MAX_LIMBS];
+    uint64_t p_special, t, zeta_t;   /* zeta_t: the slot root (smallest x with x^N = -1 mod t) */
+    uint64_t k1, kg;                 /* Galois elements of left rotation by 1 and by g */
+    uint64_t ct_words;               /* 2*L*N */
+    uint64_t keys_words;             /* 2*L*2*(L+1)*N */
+    uint64_t total_chunks;           /* sum over clusters of their chunk counts */
+    uint64_t cluster_bytes;          /* device bytes of the encoded clusters */
+    uint32_t max_wave;
+} wally_info;
+
+/* Derive primes, roots and NTT tables for `params` on `params->device` and
+ * return a new context in *out.  Allocates only the tables (a few MB).
+ * Errors: WALLY_EINVAL (unsupported sizes), WALLY_ECUDA, WALLY_ENOMEM. */
+int wally_setup_params(const wally_params *params, wally_ctx **out);
+
+/* Free the context and every device buffer it owns.  NULL is accepted. */
+void wally_destroy(wally_ctx *ctx);
+
+int wally_query_info(const wally_ctx *ctx, wally_info *out);
+
+/* Server initialisation (Alg. "Server Initialization", Sec. 5): encode every
+ * cluster into its plaintext set and keep it resident in device memory in NTT
+ * form.  Cluster c has sizes[c] embeddings (rows of `embeddings`, host, int8
+ * [sum sizes][dim], clusters back to back in id order).  Per cluster,
+ * m = max(1, ceil(size/N)) chunks of g*h plaintexts; chunk k, slot
+ * s = beta*d_pad + x holds embedding k*N + s, and plaintext (i, b) is diagonal
+ * g*i + b rotated right by g*i within each row (BSGS pre-rotation).  Replaces
+ * any previously loaded clusters.  Synchronises `stream` before returning.
+ * Errors: WALLY_EINVAL (m >= g: the paper uses BSGS only while the number of
+ * chunks is below sqrt(d), Sec. 5), WALLY_ENOMEM, WALLY_ECUDA. */
+int wally_load_clusters(wally_ctx *ctx, uint32_t num_clusters, const uint32_t *sizes,
+                        const int8_t *embeddings, void *stream);
+
+/* Number of chunks m of a loaded cluster (= ciphertexts in its response). */
+int wally_cluster_chunks(const wally_ctx *ctx, uint32_t cluster_id, uint32_t *m_out);
+
+/* The encoded plaintexts of one cluster, back in coefficient form, residues
+ * mod q_l: out (device) uint64_t [m][h][g][L][N].  For checking the encoder. */
+int wally_export_cluster(wally_ctx *ctx, uint32_t cluster_id, uint64_t *out, void *stream);
+
+/* Server computation for a batch (Alg. "Server Computation"; Sec. 5):
+ *   ct'[0] = ct, ct'[j] = Rot_1(ct'[j-1]) for j < g        (baby steps)
+ *   per chunk k of the query's cluster:
+ *     T_i = sum_b P'_{k,i,b} * ct'[b]                      (i < h)
+ *     S = T_{h-1}; S = Rot_g(S) + T_i for i = h-2 .. 0      (giant steps)
+ *     out chunk k = S
+ * Rot_r is the Galois automorphism X -> X^(3^r) followed by hybrid RNS key
+ * switching with one-limb digits and the special prime P (Sec. 7).
+ * Query q (0 <= q < n) names cluster cluster_ids[q], uses ciphertext
+ * cts[src] and keys galois_keys[src] with src = input_index ? input_index[q]
+ * : q, and writes its m ciphertexts to out[out_offsets[q] .. + m).
+ *   cluster_ids  device uint32_t [n]
+ *   cts          device uint64_t [*][2][L][N]
+ *   galois_keys  device uint64_t [*][2][L][2][L+1][N]
+ *   input_index  device uint32_t [n] or NULL
+ *   out_offsets  device uint64_t [n]  (chunk offsets, e.g. exclusive prefix sums of m)
+ *   out          device uint64_t [sum m][2][L][N], coefficient form, residues in [0, q_l)
+ * Asynchronous on `stream`: queries are grouped by cluster on the device and
+ * evaluated in waves of at most max_wave queries in scratch memory the
+ * context owns (allocated on first use, grown when needed).  Queries with an
+ * out-of-range cluster id produce no output and make wally_sync return
+ * WALLY_EINVAL.  Calls on one context must not overlap (the scratch is
+ * shared); use one context per concurrent stream.
+ * Errors: WALLY_EINVAL, WALLY_ESTATE (no clusters), WALLY_ENOMEM, WALLY_ECUDA. */
+int wally_eval_batch(wally_ctx *ctx, uint32_t n, const uint32_t *cluster_ids, const uint64_t *cts,
+                     const uint64_t *galois_keys, const uint32_t *input_index, const uint64_t *out_offsets,
+                     uint64_t *out, void *stream);
+
+/* wally_eval_batch with HOST buffers (same layouts; cluster_ids, input_index,
+ * out_offsets host arrays too).  Copies each wave's inputs to the device,
+ * evaluates, and copies the results back; returns when `out` is filled.
+ * Pinned host memory makes the copies asynchronous with the compute. */
+int wally_eval_batch_host(wally_ctx *ctx, uint32_t n, const uint32_t *cluster_ids, const uint64_t *cts,
+                          const uint64_t *galois_keys, const uint32_t *input_index,
+                          const uint64_t *out_offsets, uint64_t *out, void *stream);
+
+/* One rotation per ciphertext (Sec. 2 CtRotate; hybrid key switching of
+ * Sec. 7): out[i] = Rot_k(cts[i]) with key keys[i] ([L][2][L+1][N], the key of
+ * Galois element k).  k odd, 0 < k < 2N.  All device, coefficient form.
+ * Asynchronous on `stream`. */
+int wally_rotate(wally_ctx *ctx, uint32_t n, uint64_t galois_elt, const uint64_t *cts, const uint64_t *keys,
+                 uint64_t *out, void *stream);
+
+/* Wait for `stream` and report the first device-side error recorded since
+ * the previous wally_sync (and clear it). */
+int wally_sync(wally_ctx *ctx, void *stream);
+
+/* ---------------------------------------------------------------- client side
+ * Sec. 2 and Alg. "Client Query Generation".  The random numbers a client
+ * draws are inputs, so that results are reproducible:
+ *   secret   device int8_t [n][N]           ternary, in {-1, 0, 1}
+ *   key_a    device uint64_t [n][2][L][L+1][N]  uniform, row j in [0, q_j) (j = L: P)
+ *   key_e    device int8_t [n][2][L][N]     small errors
+ *   enc_a    device uint64_t [n][L][N]      uniform in [0, q_l)
+ *   enc_e    device int8_t [n][N]           small errors
+ */
+
+/* Galois keys for left rotations by 1 and by g (Sec. 7 "Reducing the request
+ * size"): for key element k with s' = sigma_k(s), digit i:
+ *   b_i = -a_i*s + e_i + [i == j] P s'  (mod q_j),   b_i = -a_i*s + e_i (mod P).
+ * galois_keys: device uint64_t [n][2][L][2][L+1][N], coefficient form. */
+int wally_keygen(wally_ctx *ctx, uint32_t n, const int8_t *secret, const uint64_t *key_a, const int8_t *key_e,
+                 uint64_t *galois_keys, void *stream);
+
+/* EncSemPt of the replicated query: queries device int8_t [n][dim] (a fake
+ * query passes zeros).  Slot beta*d_pad + x holds q[x] for x < d, 0 above.
+ * ct = (c0, c1) = (-a*s + e + Delta*m, a) with Delta = floor(Q/t) and m the
+ * slot encoding of that vector, coefficients in [0, t).
+ * cts: device uint64_t [n][2][L][N]. */
+int wally_encrypt_query(wally_ctx *ctx, uint32_t n, const int8_t *secret, const int8_t *queries,
+                        const uint64_t *enc_a, const int8_t *enc_e, uint64_t *cts, void *stream);
+
+/* Decrypt score ciphertexts (Sec. 2: m = round(t/Q * [c0 + c1*s]_Q) mod t)
+ * and decode the slots: scores device int64_t [n][N], centred into
+ * (-t/2, t/2]; ciphertext i uses secret[secret_index[i]] (NULL: secret[i]).
+ * The score of embedding k*N + s of the cluster is slot s of chunk k. */
+int wally_decrypt_scores(wally_ctx *ctx, uint32_t n, const int8_t *secret, const uint32_t *secret_index,
+                         const uint64_t *cts, int64_t *scores, void *stream);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *wally_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WALLY_H */

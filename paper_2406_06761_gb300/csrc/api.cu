@@ -1,0 +1,818 @@
+// api.cu -- the C ABI of include/wally.h: parameter set-up, the resident
+// cluster store, and the batched evaluation pipeline (Alg. "Server
+// Computation" of arXiv 2406.06761) built from the kernels in kernels.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/wally.h"
+#include "host_nt.hpp"
+#include "kernels.hpp"
+
+using namespace wally;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                                  \
+    do {                                                                                                \
+        cudaError_t e_ = (expr);                                                                        \
+        if (e_ != cudaSuccess) return fail(WALLY_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                                           __FILE__, __LINE__);                                          \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t count)
+    {
+        if (count <= n) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc((void **)&p, sizeof(T) * (count ? count : 1));
+        if (e == cudaSuccess) n = count;
+        else p = nullptr;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+}  // namespace
+
+struct wally_ctx {
+    int device = 0;
+    int num_sms = 0;
+    uint32_t N = 0, log_n = 0, L = 0, d = 0, d_pad = 0, g = 0, h = 0;
+    std::vector<uint64_t> mods;  // q_0..q_{L-1}, P, t
+    uint64_t zeta_t = 0, k1 = 0, kg = 0, k1_inv = 0, kg_inv = 0;
+    uint32_t max_wave = 1024;
+    DevParams dp{};
+    DevParams *d_dp = nullptr;
+    std::vector<void *> tables;
+    uint32_t *d_slot_pos = nullptr;
+    uint32_t *d_err = nullptr;
+
+    // cluster store
+    uint32_t num_clusters = 0, m_max = 0, ts = 0;
+    uint64_t total_chunks = 0;
+    std::vector<uint32_t> h_chunks, h_chunk0;
+    DevBuf<u64> ptxt;
+    DevBuf<u32> d_chunks, d_chunk0;
+
+    // wave workspace
+    uint32_t ws_wave = 0, ws_mmax = 0;
+    DevBuf<u64> keysN, ctp, T, S, sc, dg, u;
+    DevBuf<u32> plan_u32;
+    DevBuf<void *> plan_ptr;
+    WavePlan wp{};
+    // batch grouping
+    DevBuf<u32> counts, cstart, fill, sorted_q;
+    // host-buffer path staging
+    DevBuf<u64> stage_ct[2], stage_key[2], stage_out[2];
+    DevBuf<u32> stage_cluster[2];
+    DevBuf<void *> stage_ptrs[2];
+    // client temporaries
+    DevBuf<u64> tmp;
+
+    size_t ctw() const { return (size_t)2 * L * N; }
+    size_t keysw() const { return (size_t)2 * L * 2 * (L + 1) * N; }
+};
+
+namespace {
+
+int setup_tables(wally_ctx *c)
+{
+    const uint32_t M = c->L + 2;
+    DevParams &dp = c->dp;
+    memset(&dp, 0, sizeof(dp));
+    dp.log_n = (int)c->log_n;
+    dp.n = (int)c->N;
+    dp.L = (int)c->L;
+    dp.d = c->d;
+    dp.d_pad = c->d_pad;
+    dp.g = c->g;
+    dp.h = c->h;
+    for (uint32_t j = 0; j < M; j++) {
+        const uint64_t p = c->mods[j];
+        const uint64_t psi = (j == c->L + 1) ? c->zeta_t : root_2n(p, c->N);
+        if (!psi) return fail(WALLY_EINVAL, "no 2N-th root of unity mod %llu", (unsigned long long)p);
+        NttTables t = make_tables(p, psi, c->log_n);
+        std::vector<uint64_t> *arrs[4] = {&t.fwd, &t.fwd_s, &t.inv, &t.inv_s};
+        const u64 *dptr[4];
+        for (int a = 0; a < 4; a++) {
+            void *ptr = nullptr;
+            CUDA_TRY(cudaMalloc(&ptr, 8 * (size_t)c->N));
+            c->tables.push_back(ptr);
+            CUDA_TRY(cudaMemcpy(ptr, arrs[a]->data(), 8 * (size_t)c->N, cudaMemcpyHostToDevice));
+            dptr[a] = (const u64 *)ptr;
+        }
+        Mod &md = dp.m[j];
+        md.p = p;
+        md.two_p = 2 * p;
+        md.mont_neg_inv = mont_neg_inv(p);
+        const uint64_t r = (uint64_t)(((u128)1 << 64) % p);
+        md.r2 = mulmod_h(r, r, p);
+        md.n_inv = invmod_h(c->N % p, p);
+        md.n_inv_s = shoup_of(md.n_inv, p);
+        md.fwd = dptr[0];
+        md.fwd_s = dptr[1];
+        md.inv = dptr[2];
+        md.inv_s = dptr[3];
+    }
+    // CRT constants.  Delta = floor(Q/t) by long division of the product.
+    const uint64_t P = c->mods[c->L], t = c->mods[c->L + 1];
+    std::vector<uint64_t> Q(1, 1);
+    for (uint32_t i = 0; i < c->L; i++) Q = big_mul_small(Q, c->mods[i]);
+    std::vector<uint64_t> delta = big_div_small(Q, t, nullptr);
+    for (uint32_t j = 0; j < c->L; j++) {
+        const uint64_t q = c->mods[j];
+        dp.pinv[j] = invmod_h(P % q, q);
+        dp.pinv_s[j] = shoup_of(dp.pinv[j], q);
+        dp.pmodq[j] = P % q;
+        dp.pmodq_s[j] = shoup_of(dp.pmodq[j], q);
+        dp.delta[j] = big_mod_small(delta, q);
+        dp.delta_s[j] = shoup_of(dp.delta[j], q);
+        uint64_t qhat = 1;  // (Q/q_j) mod q_j
+        for (uint32_t i = 0; i < c->L; i++)
+            if (i != j) qhat = mulmod_h(qhat, c->mods[i] % q, q);
+        dp.theta[j] = invmod_h(qhat, q);
+        dp.theta_s[j] = shoup_of(dp.theta[j], q);
+    }
+    // slot s = rho*N/2 + col is the evaluation at zeta^(+-3^col); the NTT
+    // keeps the evaluation at zeta^(2 brv(i) + 1) in position i.
+    std::vector<uint32_t> pos(c->N);
+    const uint64_t two_n = 2 * (uint64_t)c->N;
+    uint64_t e3 = 1;
+    for (uint32_t col = 0; col < c->N / 2; col++) {
+        for (uint32_t rho = 0; rho < 2; rho++) {
+            const uint64_t e = rho ? two_n - e3 : e3;
+            uint32_t nat = (uint32_t)((e - 1) / 2), r = 0;
+            for (uint32_t b = 0; b < c->log_n; b++) r |= ((nat >> b) & 1u) << (c->log_n - 1 - b);
+            pos[rho * (c->N / 2) + col] = r;
+        }
+        e3 = (e3 * 3) % two_n;
+    }
+    CUDA_TRY(cudaMalloc(&c->d_slot_pos, 4 * (size_t)c->N));
+    CUDA_TRY(cudaMemcpy(c->d_slot_pos, pos.data(), 4 * (size_t)c->N, cudaMemcpyHostToDevice));
+    dp.slot_pos = c->d_slot_pos;
+    CUDA_TRY(cudaMalloc(&c->d_dp, sizeof(DevParams)));
+    dp.self = c->d_dp;
+    CUDA_TRY(cudaMemcpy(c->d_dp, &dp, sizeof(DevParams), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&c->d_err, 4));
+    CUDA_TRY(cudaMemset(c->d_err, 0, 4));
+    CUDA_TRY(set_kernel_attributes((int)c->log_n, c->g));
+    return WALLY_OK;
+}
+
+uint64_t inv_mod_2n(uint64_t k, uint64_t two_n)
+{
+    for (uint64_t x = 1; x < two_n; x += 2)
+        if ((k * x) % two_n == 1) return x;
+    return 0;
+}
+
+// Wave workspace for W queries and up to W * m_max (query, chunk) pairs.
+int ensure_workspace(wally_ctx *c, uint32_t W, uint32_t m_max)
+{
+    if (c->ws_wave >= W && c->ws_mmax >= m_max && c->keysN.p) return WALLY_OK;
+    W = std::max(W, c->ws_wave);
+    m_max = std::max(m_max, std::max(c->ws_mmax, 1u));
+    const size_t ctw = c->ctw(), keysw = c->keysw(), N = c->N, L = c->L;
+    const size_t pairs = (size_t)W * m_max;
+    c->keysN.release();
+    c->ctp.release();
+    c->T.release();
+    c->S.release();
+    c->sc.release();
+    c->dg.release();
+    c->u.release();
+    const size_t items = std::max(pairs, (size_t)W);
+    if (c->keysN.ensure(W * keysw) != cudaSuccess || c->ctp.ensure(W * (size_t)c->g * ctw) != cudaSuccess ||
+        c->T.ensure(pairs * c->h * ctw) != cudaSuccess || c->S.ensure(items * ctw) != cudaSuccess ||
+        c->sc.ensure(items * ctw) != cudaSuccess || c->dg.ensure(items * L * N) != cudaSuccess ||
+        c->u.ensure(items * 2 * (L + 1) * N) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the wave workspace (%u queries, %u chunks max)", W, m_max);
+    // plan arrays: counts[4] | cluster[W] | pair_pos[P] | pair_k[P] | pair_off[W+1] | seg x3 [W]
+    const size_t n32 = 4 + W + 2 * pairs + (W + 1) + 3 * (size_t)W;
+    if (c->plan_u32.ensure(n32) != cudaSuccess || c->plan_ptr.ensure(3 * (size_t)W) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the wave plan");
+    u32 *b = c->plan_u32.p;
+    WavePlan &wp = c->wp;
+    wp.counts = b;
+    b += 4;
+    wp.cluster = b;
+    b += W;
+    wp.pair_pos = b;
+    b += pairs;
+    wp.pair_k = b;
+    b += pairs;
+    wp.pair_off = b;
+    b += W + 1;
+    wp.seg_cluster = b;
+    b += W;
+    wp.seg_begin = b;
+    b += W;
+    wp.seg_end = b;
+    void **pp = c->plan_ptr.p;
+    wp.src_ct = (const u64 **)pp;
+    wp.src_key = (const u64 **)(pp + W);
+    wp.dst_out = (u64 **)(pp + 2 * (size_t)W);
+    c->ws_wave = W;
+    c->ws_mmax = m_max;
+    return WALLY_OK;
+}
+
+ClusterStore cluster_store(const wally_ctx *c)
+{
+    ClusterStore cs;
+    cs.ptxt = c->ptxt.p;
+    cs.chunk0 = c->d_chunk0.p;
+    cs.chunks = c->d_chunks.p;
+    cs.ts = c->ts;
+    return cs;
+}
+
+RotArgs rot_args(wally_ctx *c)
+{
+    RotArgs a;
+    memset(&a, 0, sizeof(a));
+    a.sc = c->sc.p;
+    a.dg = c->dg.p;
+    a.u = c->u.p;
+    return a;
+}
+
+// Steps a1-a5 for one wave whose plan inputs (counts[0], cluster, src_ct,
+// src_key, dst_out of wp) are already on the device, in stream order.
+int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t st)
+{
+    const DevParams &dp = c->dp;
+    const size_t ctw = c->ctw(), keysw = c->keysw();
+    const uint32_t L = c->L, g = c->g, h = c->h;
+    CUDA_TRY(launch_wave_plan(wp, c->d_chunks.p, wave_len, st));
+    // a1: ciphertexts into slot 0 of the baby-step array, keys (Montgomery)
+    CUDA_TRY(launch_to_ntt(dp, wp.src_ct, nullptr, 0, c->ctp.p, (size_t)g * ctw, 2 * L, L, wave_len, wp.counts,
+                           false, st));
+    CUDA_TRY(launch_to_ntt(dp, wp.src_key, nullptr, 0, c->keysN.p, keysw, 4 * L * (L + 1), L + 1, wave_len,
+                           wp.counts, true, st));
+    // a2: ct'[j] = Rot_1(ct'[j-1])
+    for (uint32_t j = 1; j < g; j++) {
+        RotArgs a = rot_args(c);
+        a.src = c->ctp.p + (size_t)(j - 1) * ctw;
+        a.src_stride = (size_t)g * ctw;
+        a.dst = c->ctp.p + (size_t)j * ctw;
+        a.dst_stride = (size_t)g * ctw;
+        a.key = c->keysN.p;
+        a.key_stride = keysw;
+        a.n_max = wave_len;
+        a.n_dev = wp.counts;
+        a.galois = c->k1;
+        CUDA_TRY(launch_rotate(dp, a, st));
+    }
+    // a3: T_i = sum_b P'_{k,i,b} ct'[b]
+    CUDA_TRY(launch_mac(dp, cluster_store(c), wp, c->ctp.p, c->T.p, wave_len, c->m_max, c->num_sms, st));
+    // a4: S = T_{h-1}; S = Rot_g(S) + T_i, i = h-2 .. 0
+    const uint32_t np_max = wave_len * c->m_max;
+    for (int i = (int)h - 2; i >= 0; i--) {
+        RotArgs a = rot_args(c);
+        if (i == (int)h - 2) {
+            a.src = c->T.p + (size_t)(h - 1) * ctw;
+            a.src_stride = (size_t)h * ctw;
+        } else {
+            a.src = c->S.p;
+            a.src_stride = ctw;
+        }
+        a.dst = c->S.p;
+        a.dst_stride = ctw;
+        a.add = c->T.p + (size_t)i * ctw;
+        a.add_stride = (size_t)h * ctw;
+        a.key = c->keysN.p + keysw / 2;
+        a.key_stride = keysw;
+        a.key_map = wp.pair_pos;
+        a.n_max = np_max;
+        a.n_dev = wp.counts + 1;
+        a.galois = c->kg;
+        CUDA_TRY(launch_rotate(dp, a, st));
+    }
+    // a5: back to coefficient form, into the caller's output
+    if (h == 1) CUDA_TRY(launch_output(dp, wp, c->T.p, ctw, np_max, st));
+    else CUDA_TRY(launch_output(dp, wp, c->S.p, ctw, np_max, st));
+    return WALLY_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *wally_last_error(void) { return g_err.c_str(); }
+
+int wally_setup_params(const wally_params *prm, wally_ctx **out)
+{
+    if (!prm || !out) return fail(WALLY_EINVAL, "null argument");
+    *out = nullptr;
+    if (prm->log_n < 12 || prm->log_n > 14) return fail(WALLY_EINVAL, "log_n must be 12, 13 or 14");
+    if (prm->num_q < 1 || prm->num_q >= WALLY_MAX_LIMBS) return fail(WALLY_EINVAL, "num_q out of range");
+    if (prm->q_bits < 20 || prm->q_bits > 61) return fail(WALLY_EINVAL, "q_bits out of range");
+    if (prm->t_bits < 2 || prm->t_bits > 30) return fail(WALLY_EINVAL, "t_bits out of range");
+    if (prm->dim < 1) return fail(WALLY_EINVAL, "dim must be positive");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || prm->device < 0 || prm->device >= ndev)
+        return fail(WALLY_ECUDA, "CUDA device %d not available", prm->device);
+    DeviceGuard guard(prm->device);
+    wally_ctx *c = new wally_ctx();
+    c->device = prm->device;
+    c->log_n = prm->log_n;
+    c->N = 1u << prm->log_n;
+    c->L = prm->num_q;
+    const uint64_t step = 2 * (uint64_t)c->N;
+    uint64_t below = (uint64_t)1 << prm->q_bits;
+    for (uint32_t i = 0; i < c->L; i++) {
+        uint64_t q = prm->q ? prm->q[i] : prime_1mod_below(below, step);
+        if (!q || !is_prime_u64(q) || q % step != 1) {
+            delete c;
+            return fail(WALLY_EINVAL, "no usable prime for limb %u", i);
+        }
+        c->mods.push_back(q);
+        below = q;
+    }
+    uint64_t P = prm->p_special ? prm->p_special : prime_1mod_below(below, step);
+    uint64_t t = prm->t ? prm->t : prime_1mod_below((uint64_t)1 << prm->t_bits, step);
+    if (!P || !is_prime_u64(P) || P % step != 1 || !t || !is_prime_u64(t) || t % step != 1) {
+        delete c;
+        return fail(WALLY_EINVAL, "no usable special prime or plaintext modulus");
+    }
+    c->mods.push_back(P);
+    c->mods.push_back(t);
+    // the kernels feed residues of one modulus directly into transforms mod
+    // another: every pair of ciphertext / special primes within a factor 2
+    for (uint32_t a = 0; a <= c->L; a++)
+        for (uint32_t b = 0; b <= c->L; b++)
+            if (c->mods[a] >= 2 * c->mods[b]) {
+                delete c;
+                return fail(WALLY_EINVAL, "ciphertext and special primes must be within a factor of 2");
+            }
+    c->zeta_t = smallest_root_2n(t, c->N);
+    c->d = prm->dim;
+    uint32_t dp = 1, lg = 0;
+    while (dp < prm->dim) { dp <<= 1; lg++; }
+    c->d_pad = dp;
+    c->g = 1u << ((lg + 1) / 2);
+    c->h = dp / c->g;
+    if (c->d_pad > c->N / 2 || c->d_pad > 1024 || c->g < 2) {
+        delete c;
+        return fail(WALLY_EINVAL, "dimension %u unsupported (d_pad must be 4..min(1024, N/2))", prm->dim);
+    }
+    c->k1 = 3;
+    c->kg = powmod_h(3, c->g, step);
+    c->k1_inv = inv_mod_2n(c->k1, step);
+    c->kg_inv = inv_mod_2n(c->kg, step);
+    c->max_wave = prm->max_wave ? prm->max_wave : 1024;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    int rc = setup_tables(c);
+    if (rc != WALLY_OK) {
+        std::string msg = g_err;
+        wally_destroy(c);
+        g_err = msg;
+        return rc;
+    }
+    *out = c;
+    return WALLY_OK;
+}
+
+void wally_destroy(wally_ctx *c)
+{
+    if (!c) return;
+    DeviceGuard guard(c->device);
+    for (void *p : c->tables) cudaFree(p);
+    if (c->d_slot_pos) cudaFree(c->d_slot_pos);
+    if (c->d_dp) cudaFree(c->d_dp);
+    if (c->d_err) cudaFree(c->d_err);
+    c->ptxt.release();
+    c->d_chunks.release();
+    c->d_chunk0.release();
+    c->keysN.release();
+    c->ctp.release();
+    c->T.release();
+    c->S.release();
+    c->sc.release();
+    c->dg.release();
+    c->u.release();
+    c->plan_u32.release();
+    c->plan_ptr.release();
+    c->counts.release();
+    c->cstart.release();
+    c->fill.release();
+    c->sorted_q.release();
+    for (int b = 0; b < 2; b++) {
+        c->stage_ct[b].release();
+        c->stage_key[b].release();
+        c->stage_out[b].release();
+        c->stage_cluster[b].release();
+        c->stage_ptrs[b].release();
+    }
+    c->tmp.release();
+    delete c;
+}
+
+int wally_query_info(const wally_ctx *c, wally_info *o)
+{
+    if (!c || !o) return fail(WALLY_EINVAL, "null argument");
+    memset(o, 0, sizeof(*o));
+    o->n = c->N;
+    o->log_n = c->log_n;
+    o->num_q = c->L;
+    o->dim = c->d;
+    o->d_pad = c->d_pad;
+    o->g = c->g;
+    o->h = c->h;
+    o->num_clusters = c->num_clusters;
+    for (uint32_t i = 0; i < c->L; i++) o->q[i] = c->mods[i];
+    o->p_special = c->mods[c->L];
+    o->t = c->mods[c->L + 1];
+    o->zeta_t = c->zeta_t;
+    o->k1 = c->k1;
+    o->kg = c->kg;
+    o->ct_words = c->ctw();
+    o->keys_words = c->keysw();
+    o->total_chunks = c->total_chunks;
+    o->cluster_bytes = c->ptxt.n * 8;
+    o->max_wave = c->max_wave;
+    return WALLY_OK;
+}
+
+int wally_load_clusters(wally_ctx *c, uint32_t K, const uint32_t *sizes, const int8_t *emb, void *stream)
+{
+    if (!c || (K && !sizes)) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<uint32_t> chunks(K), chunk0(K);
+    std::vector<uint64_t> row0(K);
+    uint64_t rows = 0, Z = 0;
+    uint32_t m_max = 1;
+    for (uint32_t i = 0; i < K; i++) {
+        uint32_t m = std::max<uint32_t>(1, (sizes[i] + c->N - 1) / c->N);
+        if (m >= c->g)
+            return fail(WALLY_EINVAL, "cluster %u needs %u chunks; BSGS needs fewer than g = %u", i, m, c->g);
+        chunks[i] = m;
+        chunk0[i] = (uint32_t)Z;
+        row0[i] = rows;
+        rows += sizes[i];
+        Z += m;
+        m_max = std::max(m_max, m);
+    }
+    if (rows && !emb) return fail(WALLY_EINVAL, "null embeddings");
+    // tile width: one tile of d_pad * ts words is 64 KB of shared memory
+    uint32_t ts = std::max<uint32_t>(1, 8192 / c->d_pad);
+    ts = std::min<uint32_t>(ts, 64);
+    const size_t words = (size_t)Z * c->L * c->N * c->d_pad;
+    c->ptxt.release();
+    c->num_clusters = 0;
+    if (c->ptxt.ensure(words) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate %.1f GB for the encoded clusters", words * 8.0 / 1e9);
+    std::vector<uint32_t> chunk_cluster(Z), chunk_k(Z);
+    for (uint32_t i = 0; i < K; i++)
+        for (uint32_t k = 0; k < chunks[i]; k++) {
+            chunk_cluster[chunk0[i] + k] = i;
+            chunk_k[chunk0[i] + k] = k;
+        }
+    int8_t *d_emb = nullptr;
+    u64 *d_row0 = nullptr;
+    u32 *d_size = nullptr, *d_cc = nullptr, *d_ck = nullptr;
+    CUDA_TRY(cudaMalloc(&d_emb, std::max<size_t>(1, rows * c->d)));
+    CUDA_TRY(cudaMalloc(&d_row0, 8 * std::max<size_t>(1, K)));
+    CUDA_TRY(cudaMalloc(&d_size, 4 * std::max<size_t>(1, K)));
+    CUDA_TRY(cudaMalloc(&d_cc, 4 * std::max<size_t>(1, Z)));
+    CUDA_TRY(cudaMalloc(&d_ck, 4 * std::max<size_t>(1, Z)));
+    if (rows) CUDA_TRY(cudaMemcpyAsync(d_emb, emb, rows * c->d, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_row0, row0.data(), 8 * (size_t)K, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_size, sizes, 4 * (size_t)K, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_cc, chunk_cluster.data(), 4 * (size_t)Z, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_ck, chunk_k.data(), 4 * (size_t)Z, cudaMemcpyHostToDevice, st));
+    for (uint64_t z0 = 0; z0 < Z; z0 += 65535) {
+        EncodeArgs a;
+        a.emb = d_emb;
+        a.row0 = d_row0;
+        a.size = d_size;
+        a.chunk_cluster = d_cc + z0;
+        a.chunk_k = d_ck + z0;
+        a.total_chunks = (uint32_t)std::min<uint64_t>(65535, Z - z0);
+        a.ptxt = c->ptxt.p + z0 * c->L * c->N * c->d_pad;
+        a.ts = ts;
+        CUDA_TRY(launch_encode_clusters(c->dp, a, st));
+    }
+    if (c->d_chunks.ensure(std::max<uint32_t>(K, 1)) != cudaSuccess ||
+        c->d_chunk0.ensure(std::max<uint32_t>(K, 1)) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the cluster index");
+    CUDA_TRY(cudaMemcpyAsync(c->d_chunks.p, chunks.data(), 4 * (size_t)K, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(c->d_chunk0.p, chunk0.data(), 4 * (size_t)K, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(d_emb);
+    cudaFree(d_row0);
+    cudaFree(d_size);
+    cudaFree(d_cc);
+    cudaFree(d_ck);
+    c->num_clusters = K;
+    c->m_max = m_max;
+    c->ts = ts;
+    c->total_chunks = Z;
+    c->h_chunks = chunks;
+    c->h_chunk0 = chunk0;
+    return WALLY_OK;
+}
+
+int wally_cluster_chunks(const wally_ctx *c, uint32_t id, uint32_t *m_out)
+{
+    if (!c || !m_out) return fail(WALLY_EINVAL, "null argument");
+    if (id >= c->num_clusters) return fail(WALLY_EINVAL, "cluster id %u out of range (%u clusters)", id, c->num_clusters);
+    *m_out = c->h_chunks[id];
+    return WALLY_OK;
+}
+
+int wally_export_cluster(wally_ctx *c, uint32_t id, uint64_t *out, void *stream)
+{
+    if (!c || !out) return fail(WALLY_EINVAL, "null argument");
+    if (id >= c->num_clusters) return fail(WALLY_EINVAL, "cluster id %u out of range", id);
+    DeviceGuard guard(c->device);
+    CUDA_TRY(launch_export_cluster(c->dp, cluster_store(c), id, c->h_chunks[id], out, (cudaStream_t)stream));
+    return WALLY_OK;
+}
+
+int wally_eval_batch(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
+                     const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (!c->num_clusters) return fail(WALLY_ESTATE, "no clusters loaded");
+    if (n == 0) return WALLY_OK;
+    if (!ids || !cts || !keys || !out_offsets || !out) return fail(WALLY_EINVAL, "null argument");
+    if (!aligned16(cts) || !aligned16(keys) || !aligned16(out)) return fail(WALLY_EINVAL, "buffers must be 16-byte aligned");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t W = c->max_wave;
+    int rc = ensure_workspace(c, W, c->m_max);
+    if (rc) return rc;
+    const uint32_t K = c->num_clusters;
+    if (c->counts.ensure(K) != cudaSuccess || c->cstart.ensure(K + 1) != cudaSuccess ||
+        c->fill.ensure(K) != cudaSuccess || c->sorted_q.ensure(n) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the grouping arrays");
+    // a0: group by cluster
+    CUDA_TRY(launch_group(ids, n, K, c->counts.p, c->cstart.p, c->fill.p, c->sorted_q.p, c->d_err, st));
+    for (uint32_t wb = 0; wb < n; wb += W) {
+        const uint32_t len = std::min(W, n - wb);
+        CUDA_TRY(launch_gather_wave(c->wp, c->sorted_q.p, ids, c->cstart.p, K, wb, len, cts, keys, input_index,
+                                    out_offsets, out, c->ctw(), c->keysw(), st));
+        rc = run_wave(c, c->wp, len, st);
+        if (rc) return rc;
+    }
+    return WALLY_OK;
+}
+
+int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
+                          const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (!c->num_clusters) return fail(WALLY_ESTATE, "no clusters loaded");
+    if (n == 0) return WALLY_OK;
+    if (!ids || !cts || !keys || !out_offsets || !out) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t K = c->num_clusters, W = c->max_wave;
+    for (uint32_t q = 0; q < n; q++)
+        if (ids[q] >= K) return fail(WALLY_EINVAL, "query %u names cluster %u of %u", q, ids[q], K);
+    int rc = ensure_workspace(c, W, c->m_max);
+    if (rc) return rc;
+    const size_t ctw = c->ctw(), keysw = c->keysw();
+    for (int b = 0; b < 2; b++) {
+        if (c->stage_ct[b].ensure((size_t)W * ctw) != cudaSuccess ||
+            c->stage_key[b].ensure((size_t)W * keysw) != cudaSuccess ||
+            c->stage_out[b].ensure((size_t)W * c->m_max * ctw) != cudaSuccess ||
+            c->stage_cluster[b].ensure(W + 4) != cudaSuccess || c->stage_ptrs[b].ensure(3 * (size_t)W) != cudaSuccess)
+            return fail(WALLY_ENOMEM, "cannot allocate the staging buffers");
+    }
+    // host-side grouping by cluster (counting sort; stable)
+    std::vector<uint32_t> start(K + 1, 0), order(n);
+    for (uint32_t q = 0; q < n; q++) start[ids[q] + 1]++;
+    for (uint32_t k = 0; k < K; k++) start[k + 1] += start[k];
+    {
+        std::vector<uint32_t> fillh(start.begin(), start.end() - 1);
+        for (uint32_t q = 0; q < n; q++) order[fillh[ids[q]]++] = q;
+    }
+    cudaStream_t cin = nullptr, cout_ = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&cout_, cudaStreamNonBlocking));
+    cudaEvent_t in_done[2], comp_done[2], out_done[2];
+    for (int b = 0; b < 2; b++) {
+        CUDA_TRY(cudaEventCreateWithFlags(&in_done[b], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&comp_done[b], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&out_done[b], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(comp_done[b], st));
+        CUDA_TRY(cudaEventRecord(out_done[b], st));
+    }
+    // per-buffer host copies of the plan inputs (pinned so the uploads are async)
+    std::vector<uint32_t *> h_plan32(2, nullptr);
+    std::vector<void **> h_planptr(2, nullptr);
+    for (int b = 0; b < 2; b++) {
+        CUDA_TRY(cudaMallocHost(&h_plan32[b], 4 * ((size_t)W + 4)));
+        CUDA_TRY(cudaMallocHost(&h_planptr[b], sizeof(void *) * 3 * (size_t)W));
+    }
+    std::vector<uint32_t> pair_off(W + 1);
+    int wave = 0;
+    rc = WALLY_OK;
+    for (uint32_t wb = 0; wb < n && rc == WALLY_OK; wb += W, wave++) {
+        const int b = wave & 1;
+        const uint32_t len = std::min(W, n - wb);
+        // buffer b is free once the compute and the read-back of wave - 2 are done
+        if (cudaEventSynchronize(comp_done[b]) != cudaSuccess) { rc = fail(WALLY_ECUDA, "event sync"); break; }
+        uint32_t *p32 = h_plan32[b];
+        void **pp = h_planptr[b];
+        p32[0] = len;
+        p32[1] = p32[2] = p32[3] = 0;
+        pair_off[0] = 0;
+        for (uint32_t i = 0; i < len; i++) {
+            const uint32_t q = order[wb + i];
+            const uint32_t src = input_index ? input_index[q] : q;
+            p32[4 + i] = ids[q];
+            pair_off[i + 1] = pair_off[i] + c->h_chunks[ids[q]];
+            pp[i] = c->stage_ct[b].p + (size_t)i * ctw;
+            pp[W + i] = c->stage_key[b].p + (size_t)i * keysw;
+            pp[2 * (size_t)W + i] = c->stage_out[b].p + (size_t)pair_off[i] * ctw;
+            if (cudaMemcpyAsync(c->stage_ct[b].p + (size_t)i * ctw, cts + (size_t)src * ctw, 8 * ctw,
+                                cudaMemcpyHostToDevice, cin) != cudaSuccess ||
+                cudaMemcpyAsync(c->stage_key[b].p + (size_t)i * keysw, keys + (size_t)src * keysw, 8 * keysw,
+                                cudaMemcpyHostToDevice, cin) != cudaSuccess) {
+                rc = fail(WALLY_ECUDA, "input copy failed");
+                break;
+            }
+        }
+        if (rc) break;
+        WavePlan wp = c->wp;
+        wp.counts = c->stage_cluster[b].p;
+        wp.cluster = c->stage_cluster[b].p + 4;
+        wp.src_ct = (const u64 **)c->stage_ptrs[b].p;
+        wp.src_key = (const u64 **)(c->stage_ptrs[b].p + W);
+        wp.dst_out = (u64 **)(c->stage_ptrs[b].p + 2 * (size_t)W);
+        CUDA_TRY(cudaMemcpyAsync(wp.counts, p32, 4 * ((size_t)len + 4), cudaMemcpyHostToDevice, cin));
+        CUDA_TRY(cudaMemcpyAsync(c->stage_ptrs[b].p, pp, sizeof(void *) * 3 * (size_t)W, cudaMemcpyHostToDevice, cin));
+        CUDA_TRY(cudaEventRecord(in_done[b], cin));
+        CUDA_TRY(cudaStreamWaitEvent(st, in_done[b], 0));
+        CUDA_TRY(cudaStreamWaitEvent(st, out_done[b], 0));
+        rc = run_wave(c, wp, len, st);
+        if (rc) break;
+        CUDA_TRY(cudaEventRecord(comp_done[b], st));
+        CUDA_TRY(cudaStreamWaitEvent(cout_, comp_done[b], 0));
+        for (uint32_t i = 0; i < len; i++) {
+            const uint32_t q = order[wb + i];
+            const uint32_t m = c->h_chunks[ids[q]];
+            if (cudaMemcpyAsync(out + out_offsets[q] * ctw, c->stage_out[b].p + (size_t)pair_off[i] * ctw,
+                                8 * ctw * m, cudaMemcpyDeviceToHost, cout_) != cudaSuccess) {
+                rc = fail(WALLY_ECUDA, "output copy failed");
+                break;
+            }
+        }
+        CUDA_TRY(cudaEventRecord(out_done[b], cout_));
+    }
+    cudaStreamSynchronize(cin);
+    cudaStreamSynchronize(cout_);
+    cudaStreamSynchronize(st);
+    for (int b = 0; b < 2; b++) {
+        cudaEventDestroy(in_done[b]);
+        cudaEventDestroy(comp_done[b]);
+        cudaEventDestroy(out_done[b]);
+        cudaFreeHost(h_plan32[b]);
+        cudaFreeHost(h_planptr[b]);
+    }
+    cudaStreamDestroy(cin);
+    cudaStreamDestroy(cout_);
+    return rc;
+}
+
+int wally_rotate(wally_ctx *c, uint32_t n, uint64_t k, const uint64_t *cts, const uint64_t *keys, uint64_t *out,
+                 void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0) return WALLY_OK;
+    if (!cts || !keys || !out) return fail(WALLY_EINVAL, "null argument");
+    if ((k & 1) == 0 || k >= 2 * (uint64_t)c->N) return fail(WALLY_EINVAL, "Galois element must be odd and < 2N");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_workspace(c, c->max_wave, std::max<uint32_t>(c->m_max, 1));
+    if (rc) return rc;
+    const size_t ctw = c->ctw(), keyw = c->keysw() / 2;
+    const uint32_t chunk = c->max_wave;
+    for (uint32_t x0 = 0; x0 < n; x0 += chunk) {
+        const uint32_t cnt = std::min(chunk, n - x0);
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, cts + (size_t)x0 * ctw, ctw, c->S.p, ctw, 2 * c->L, c->L, cnt, nullptr,
+                               false, st));
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)x0 * keyw, keyw, c->keysN.p, keyw,
+                               2 * c->L * (c->L + 1), c->L + 1, cnt, nullptr, true, st));
+        RotArgs a = rot_args(c);
+        a.src = c->S.p;
+        a.src_stride = ctw;
+        a.dst = c->S.p;
+        a.dst_stride = ctw;
+        a.key = c->keysN.p;
+        a.key_stride = keyw;
+        a.n_max = cnt;
+        a.galois = k;
+        CUDA_TRY(launch_rotate(c->dp, a, st));
+        CUDA_TRY(launch_from_ntt(c->dp, c->S.p, out + (size_t)x0 * ctw, 2 * c->L, c->L, cnt, st));
+    }
+    return WALLY_OK;
+}
+
+int wally_sync(wally_ctx *c, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    uint32_t err = 0;
+    CUDA_TRY(cudaMemcpy(&err, c->d_err, 4, cudaMemcpyDeviceToHost));
+    if (err) {
+        CUDA_TRY(cudaMemset(c->d_err, 0, 4));
+        return fail(WALLY_EINVAL, "a query named a cluster id out of range");
+    }
+    return WALLY_OK;
+}
+
+int wally_keygen(wally_ctx *c, uint32_t n, const int8_t *secret, const uint64_t *key_a, const int8_t *key_e,
+                 uint64_t *keys, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0) return WALLY_OK;
+    if (!secret || !key_a || !key_e || !keys) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(launch_keygen(c->dp, secret, key_a, key_e, n, c->k1, c->kg, c->k1_inv, c->kg_inv, keys,
+                           (cudaStream_t)stream));
+    return WALLY_OK;
+}
+
+int wally_encrypt_query(wally_ctx *c, uint32_t n, const int8_t *secret, const int8_t *queries, const uint64_t *enc_a,
+                        const int8_t *enc_e, uint64_t *cts, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0) return WALLY_OK;
+    if (!secret || !queries || !enc_a || !enc_e || !cts) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the temporary is shared by the client calls of this context: order them
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (c->tmp.ensure((size_t)n * c->N) != cudaSuccess) return fail(WALLY_ENOMEM, "temporary");
+    CUDA_TRY(launch_encode_queries(c->dp, queries, n, c->tmp.p, st));
+    CUDA_TRY(launch_encrypt(c->dp, secret, c->tmp.p, enc_a, enc_e, n, cts, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return WALLY_OK;
+}
+
+int wally_decrypt_scores(wally_ctx *c, uint32_t n, const int8_t *secret, const uint32_t *secret_index,
+                         const uint64_t *cts, int64_t *scores, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0) return WALLY_OK;
+    if (!secret || !cts || !scores) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (c->tmp.ensure((size_t)n * c->L * c->N) != cudaSuccess) return fail(WALLY_ENOMEM, "temporary");
+    CUDA_TRY(launch_decrypt(c->dp, secret, secret_index, cts, n, c->tmp.p, scores, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return WALLY_OK;
+}
+
+}  // extern "C"

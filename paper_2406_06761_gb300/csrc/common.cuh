@@ -1,0 +1,248 @@
+// common.cuh -- device-side building blocks of the Wally GB300 library:
+// RNS modular arithmetic on 64-bit residues (primes below 2^61) and the
+// negacyclic NTT of one polynomial held in shared memory by one CTA.
+//
+// Modular arithmetic follows published methods:
+//  - Shoup's precomputed-quotient multiplication for constant operands
+//    (twiddles, P^-1, Delta): w' = floor(w * 2^64 / p), q = hi64(x * w'),
+//    r = x*w - q*p in [0, 2p) for any x < 2^64.
+//  - Montgomery reduction (Montgomery 1985) with R = 2^64 for variable
+//    products: operands stored pre-multiplied by R (keys, plaintexts), a
+//    128-bit sum T < p * 2^64 reduces to T * R^-1 mod p with one REDC.  Lazy
+//    sums of up to 2^12 products of residues < p (Sec. 7 "lazy reduction" in
+//    sequential plaintext-ciphertext products) stay below that bound.
+//  - Harvey's lazy butterflies (Harvey 2014, the NTT the paper's library uses,
+//    Sec. 7): forward Cooley-Tukey values in [0, 4p), inverse Gentleman-Sande
+//    values in [0, 2p).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef uint64_t u64;
+typedef unsigned int u32;
+
+#ifndef WALLY_MAX_LIMBS
+#define WALLY_MAX_LIMBS 8
+#endif
+#define WALLY_MAX_MODS (WALLY_MAX_LIMBS + 2)
+
+// One RNS modulus with its NTT tables (device pointers, N entries each).
+// fwd[k] = psi^brv(k), inv[k] = psi^-brv(k), brv = bit reversal on log2 N bits.
+struct Mod {
+    u64 p, two_p;
+    u64 mont_neg_inv;  // -p^-1 mod 2^64
+    u64 r2;            // 2^128 mod p
+    u64 n_inv, n_inv_s;
+    const u64 *fwd, *fwd_s, *inv, *inv_s;
+};
+
+// Everything a kernel needs about the parameter set, passed by value.
+// Modulus index j: 0..L-1 ciphertext primes q_j, L = P, L+1 = t.
+struct DevParams {
+    int log_n, n, L;
+    u32 d, d_pad, g, h;
+    Mod m[WALLY_MAX_MODS];
+    u64 pinv[WALLY_MAX_LIMBS], pinv_s[WALLY_MAX_LIMBS];    // P^-1 mod q_j
+    u64 pmodq[WALLY_MAX_LIMBS], pmodq_s[WALLY_MAX_LIMBS];  // P mod q_j
+    u64 delta[WALLY_MAX_LIMBS], delta_s[WALLY_MAX_LIMBS];  // [floor(Q/t)]_{q_j}
+    u64 theta[WALLY_MAX_LIMBS], theta_s[WALLY_MAX_LIMBS];  // [(Q/q_j)^-1]_{q_j}
+    const u32 *slot_pos;      // [N] NTT position (mod t) of slot s
+    const DevParams *self;    // device copy of this block (kernels read it there)
+};
+
+__device__ __forceinline__ u64 csub(u64 x, u64 m) { return x >= m ? x - m : x; }
+
+// x * w mod p up to one p: result in [0, 2p).  Requires p < 2^63.
+__device__ __forceinline__ u64 shoup_mul(u64 x, u64 w, u64 ws, u64 p)
+{
+    u64 q = __umul64hi(x, ws);
+    return x * w - q * p;
+}
+
+// (hi * 2^64 + lo) * 2^-64 mod p, for hi < p; canonical result.
+__device__ __forceinline__ u64 mont_redc(u64 hi, u64 lo, const Mod &md)
+{
+    u64 m = lo * md.mont_neg_inv;
+    u64 mh = __umul64hi(m, md.p);
+    return csub(hi + mh + (lo != 0 ? 1ull : 0ull), md.p);
+}
+
+// a * b * 2^-64 mod p for a * b < p * 2^64 (e.g. a < 4p, b < p).
+__device__ __forceinline__ u64 mont_mul(u64 a, u64 b, const Mod &md)
+{
+    return mont_redc(__umul64hi(a, b), a * b, md);
+}
+
+// Plain a * b mod p for canonical a, b (two REDCs).
+__device__ __forceinline__ u64 mulmod(u64 a, u64 b, const Mod &md)
+{
+    return mont_mul(mont_mul(a, b, md), md.r2, md);
+}
+
+// 128-bit multiply-accumulate: (hi:lo) += a * b.
+__device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b)
+{
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(lo), "+l"(hi)
+        : "l"(a), "l"(b));
+}
+
+__device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 p) { return csub(a + b, p); }
+__device__ __forceinline__ u64 submod(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + p - b; }
+
+// --------------------------------------------------------------------------- NTT
+// One CTA of N/32 threads transforms one polynomial in shared memory.  Each
+// pass loads groups of 2^R elements into registers, runs R butterfly stages,
+// and stores them back; three passes cover log2 N stages.  Shared memory is
+// padded by one word every 16 so that the stride-16 accesses of the last pass
+// do not collide in one bank.
+
+__host__ __device__ constexpr int smem_words(int n) { return n + n / 16; }
+__device__ __forceinline__ int pidx(int x) { return x + (x >> 4); }
+
+template <int LOGN>
+struct NttShape {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int T = N / 32;  // threads per CTA
+    // stage counts of the three passes
+    static constexpr int R0 = (LOGN == 12) ? 4 : 5;
+    static constexpr int R1 = (LOGN == 14) ? 5 : 4;
+    static constexpr int R2 = LOGN - R0 - R1;
+    // at most 128 registers a thread, so that two CTAs share an SM
+    static constexpr int MIN_BLOCKS = 65536 / (T * 128);
+};
+
+__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 p, u64 two_p)
+{
+    u64 x = csub(X, two_p);
+    u64 t = shoup_mul(Y, w, ws, p);
+    X = x + t;
+    Y = x - t + two_p;
+}
+
+__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 p, u64 two_p)
+{
+    u64 x = X, y = Y;
+    X = csub(x + y, two_p);
+    Y = shoup_mul(x - y + two_p, w, ws, p);
+}
+
+// One butterfly stage ST (0-based inside the pass) on the 2^R registers v of
+// a group.  Stage s = S0 + ST pairs elements 2^(LOGN-1-s) apart (2^(R-1-ST)
+// apart inside the group); the block of element x is x >> (LOGN - s) and its
+// twiddle is table[2^s + block].  All indices are compile-time constants so
+// that v stays in registers.
+template <int S0, int R, int ST, bool FWD>
+__device__ __forceinline__ void ntt_stage(u64 *v, int hi, const u64 *__restrict__ tw, const u64 *__restrict__ tws,
+                                          u64 p, u64 two_p)
+{
+    constexpr int HD = 1 << (R - 1 - ST);
+    constexpr int NB = 1 << ST;
+#pragma unroll
+    for (int blk = 0; blk < NB; blk++) {
+        const int ti = (1 << (S0 + ST)) + ((hi << ST) | blk);
+        const u64 w = __ldg(tw + ti), ws = __ldg(tws + ti);
+#pragma unroll
+        for (int j = 0; j < HD; j++) {
+            if (FWD) ct_bfly(v[blk * 2 * HD + j], v[blk * 2 * HD + j + HD], w, ws, p, two_p);
+            else gs_bfly(v[blk * 2 * HD + j], v[blk * 2 * HD + j + HD], w, ws, p, two_p);
+        }
+    }
+}
+
+template <int S0, int R, int ST>
+__device__ __forceinline__ void ntt_stages_fwd(u64 *v, int hi, const u64 *tw, const u64 *tws, u64 p, u64 two_p)
+{
+    if constexpr (ST < R) {
+        ntt_stage<S0, R, ST, true>(v, hi, tw, tws, p, two_p);
+        ntt_stages_fwd<S0, R, ST + 1>(v, hi, tw, tws, p, two_p);
+    }
+}
+
+template <int S0, int R, int ST>
+__device__ __forceinline__ void ntt_stages_inv(u64 *v, int hi, const u64 *tw, const u64 *tws, u64 p, u64 two_p)
+{
+    if constexpr (ST >= 0) {
+        ntt_stage<S0, R, ST, false>(v, hi, tw, tws, p, two_p);
+        ntt_stages_inv<S0, R, ST - 1>(v, hi, tw, tws, p, two_p);
+    }
+}
+
+// Stages S0 .. S0+R-1 of the forward transform (FWD) or, in reverse order,
+// of the inverse transform, on groups of 2^R elements held in registers.
+template <int LOGN, int S0, int R, bool FWD>
+__device__ __forceinline__ void ntt_pass(u64 *sm, const Mod &md)
+{
+    constexpr int T = NttShape<LOGN>::T;
+    constexpr int G = 1 << R;
+    constexpr int NG = 32 / G;
+    constexpr int BLO = LOGN - R - S0;
+    const int tid = threadIdx.x;
+    const u64 p = md.p, two_p = md.two_p;
+    const u64 *tw = FWD ? md.fwd : md.inv;
+    const u64 *tws = FWD ? md.fwd_s : md.inv_s;
+#pragma unroll
+    for (int u = 0; u < NG; u++) {
+        const int gi = tid + T * u;
+        const int lo = gi & ((1 << BLO) - 1);
+        const int hi = gi >> BLO;
+        const int base = (hi << (BLO + R)) | lo;
+        u64 v[G];
+#pragma unroll
+        for (int k = 0; k < G; k++) v[k] = sm[pidx(base + (k << BLO))];
+        if constexpr (FWD) ntt_stages_fwd<S0, R, 0>(v, hi, tw, tws, p, two_p);
+        else ntt_stages_inv<S0, R, R - 1>(v, hi, tw, tws, p, two_p);
+#pragma unroll
+        for (int k = 0; k < G; k++) sm[pidx(base + (k << BLO))] = v[k];
+    }
+}
+
+// Forward negacyclic NTT in place: natural-order coefficients (any values
+// < 4p) -> evaluations at psi^(2*brv(i)+1) in bit-reversed position i, values
+// in [0, 4p).  Ends with __syncthreads().
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd(u64 *sm, const Mod &md)
+{
+    using S = NttShape<LOGN>;
+    __syncthreads();
+    ntt_pass<LOGN, 0, S::R0, true>(sm, md);
+    __syncthreads();
+    ntt_pass<LOGN, S::R0, S::R1, true>(sm, md);
+    __syncthreads();
+    ntt_pass<LOGN, S::R0 + S::R1, S::R2, true>(sm, md);
+    __syncthreads();
+}
+
+// Inverse: bit-reversed evaluations (values < 2p) -> natural-order
+// coefficients times N (values in [0, 2p)); callers scale by N^-1 with
+// finish_inv().  Ends with __syncthreads().
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv(u64 *sm, const Mod &md)
+{
+    using S = NttShape<LOGN>;
+    __syncthreads();
+    ntt_pass<LOGN, S::R0 + S::R1, S::R2, false>(sm, md);
+    __syncthreads();
+    ntt_pass<LOGN, S::R0, S::R1, false>(sm, md);
+    __syncthreads();
+    ntt_pass<LOGN, 0, S::R0, false>(sm, md);
+    __syncthreads();
+}
+
+// [0, 4p) -> [0, p)
+__device__ __forceinline__ u64 fwd_finish(u64 x, const Mod &md) { return csub(csub(x, md.two_p), md.p); }
+// N^-1 scaling after ntt_inv, canonical result.
+__device__ __forceinline__ u64 inv_finish(u64 x, const Mod &md) { return csub(shoup_mul(x, md.n_inv, md.n_inv_s, md.p), md.p); }
+
+__device__ __forceinline__ u32 brv(u32 x, int log_n) { return __brev(x) >> (32 - log_n); }
+
+// Position, in the bit-reversed NTT order, of the evaluation that the Galois
+// automorphism sigma_k moves to position j: (sigma_k a)(w) = a(w^k), and
+// position j holds the evaluation at psi^(2 brv(j) + 1).
+__device__ __forceinline__ u32 galois_src(u32 j, u64 k, int log_n)
+{
+    const u32 mask2n = (2u << log_n) - 1;
+    u32 e = (u32)(((u64)(2 * brv(j, log_n) + 1) * k) & mask2n);
+    return brv((e - 1) >> 1, log_n);
+}

@@ -1,0 +1,429 @@
+// kernels_client.cu -- set-up and client-side kernels of the Wally GB300
+// library: cluster encoding (Alg. "Server Initialization"), its export back to
+// coefficient form, and the client operations of Sec. 2 / Alg. "Client Query
+// Generation" (query encoding, encryption, Galois keys, decryption).  None of
+// these is on the timed server path.
+#include "kernels.hpp"
+
+namespace wally {
+
+namespace {
+
+
+template <int LOGN>
+__device__ __forceinline__ void load_mod(Mod *s, const DevParams *dpp, int j)
+{
+    if (threadIdx.x < sizeof(Mod) / 8) ((u64 *)s)[threadIdx.x] = ((const u64 *)&dpp->m[j])[threadIdx.x];
+    __syncthreads();
+}
+
+__device__ __forceinline__ u32 item_count(u32 n_max, const u32 *n_dev)
+{
+    if (!n_dev) return n_max;
+    u32 c = *n_dev;
+    return c < n_max ? c : n_max;
+}
+
+#define NTT_LB(LOGN) __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::MIN_BLOCKS)
+#define NTT_LB_WIDE(LOGN) __launch_bounds__(NttShape<LOGN>::T)
+
+// ---------------------------------------------------------------- setup: cluster encoding
+// CTA (plaintext (i, b), global chunk z): the slot vector of P'_{k,i,b}
+// (diagonal j = g*i + b of the chunk's slices, rotated right by g*i within
+// each row; Alg. "Server Initialization", Sec. 4.1) scattered to the NTT
+// positions mod t, inverse NTT mod t (slot decoding), centred lift (reading
+// R9), then per limb: forward NTT mod q_l, times 2^64, tile layout.
+template <int LOGN>
+__global__ void NTT_LB_WIDE(LOGN) k_encode_cluster(const DevParams *dpp, EncodeArgs a)
+{
+    constexpr int N = 1 << LOGN, T = N / 32, HALF = N / 2;
+    extern __shared__ u64 sm[];
+    __shared__ Mod md;
+    const u32 z = blockIdx.y, ib = blockIdx.x;
+    const int L = dpp->L;
+    const u32 g = dpp->g, d = dpp->d, dpad = dpp->d_pad;
+    const u32 i = ib / g, b = ib % g, j = g * i + b, shift = (g * i) % HALF;
+    const u32 c = a.chunk_cluster[z], k = a.chunk_k[z], size = a.size[c];
+    const u64 row0 = a.row0[c];
+    load_mod<LOGN>(&md, dpp, L + 1);
+    const u64 t = md.p;
+#pragma unroll 4
+    for (int u = 0; u < 32; u++) {
+        const u32 s = threadIdx.x + T * u;
+        const u32 rho = s / HALF, col = s % HALF;
+        const u32 src = rho * HALF + (col + HALF - shift) % HALF;
+        const u32 xx = src % dpad, cc = (xx + j) % dpad;
+        const u64 ue = (u64)k * N + src;
+        long v = (ue < size && cc < d) ? (long)a.emb[(row0 + ue) * d + cc] : 0;
+        sm[pidx(dpp->slot_pos[s])] = v < 0 ? (u64)(v + (long)t) : (u64)v;
+    }
+    ntt_inv<LOGN>(sm, md);
+    u64 mc[32];
+#pragma unroll
+    for (int u = 0; u < 32; u++) mc[u] = inv_finish(sm[pidx(threadIdx.x + T * u)], md);
+    const u32 ts = a.ts, tiles = N / ts;
+    for (int l = 0; l < L; l++) {
+        __syncthreads();
+        load_mod<LOGN>(&md, dpp, l);
+        const u64 q = md.p;
+#pragma unroll
+        for (int u = 0; u < 32; u++) sm[pidx(threadIdx.x + T * u)] = mc[u] > (t - 1) / 2 ? q - (t - mc[u]) : mc[u];
+        ntt_fwd<LOGN>(sm, md);
+        u64 *base = a.ptxt + ((size_t)z * L + l) * tiles * ((size_t)dpad * ts);
+#pragma unroll 4
+        for (int u = 0; u < 32; u++) {
+            const u32 e = threadIdx.x + T * u;
+            u64 v = mont_mul(fwd_finish(sm[pidx(e)], md), md.r2, md);
+            base[(size_t)(e / ts) * dpad * ts + (size_t)ib * ts + e % ts] = v;
+        }
+    }
+}
+
+// Back to coefficient form: CTA (plaintext ib, limb l, chunk k of the cluster).
+template <int LOGN>
+__global__ void NTT_LB_WIDE(LOGN) k_export_cluster(const DevParams *dpp, ClusterStore cs, u32 cluster, u64 *out)
+{
+    constexpr int N = 1 << LOGN, T = N / 32;
+    extern __shared__ u64 sm[];
+    __shared__ Mod md;
+    const u32 ib = blockIdx.x, l = blockIdx.y, k = blockIdx.z;
+    const int L = dpp->L;
+    const u32 dpad = dpp->d_pad, ts = cs.ts, tiles = N / ts;
+    load_mod<LOGN>(&md, dpp, l);
+    const u32 zz = cs.chunk0[cluster] + k;
+    const u64 *base = cs.ptxt + ((size_t)zz * L + l) * tiles * ((size_t)dpad * ts);
+#pragma unroll 4
+    for (int u = 0; u < 32; u++) {
+        const u32 e = threadIdx.x + T * u;
+        sm[pidx(e)] = mont_redc(0, base[(size_t)(e / ts) * dpad * ts + (size_t)ib * ts + e % ts], md);
+    }
+    ntt_inv<LOGN>(sm, md);
+    u64 *d = out + (((size_t)k * dpad + ib) * L + l) * N;
+#pragma unroll 8
+    for (int u = 0; u < 32; u++) {
+        const u32 e = threadIdx.x + T * u;
+        d[e] = inv_finish(sm[pidx(e)], md);
+    }
+}
+
+// ---------------------------------------------------------------- client side
+// Slot vector of the replicated query (slot beta*d_pad + x holds q[x] for
+// x < d) -> plaintext polynomial mod t.
+template <int LOGN>
+__global__ void NTT_LB_WIDE(LOGN) k_encode_query(const DevParams *dpp, const int8_t *queries, u64 *m_out)
+{
+    constexpr int N = 1 << LOGN, T = N / 32;
+    extern __shared__ u64 sm[];
+    __shared__ Mod md;
+    const u32 n = blockIdx.x;
+    const int L = dpp->L;
+    const u32 d = dpp->d, dpad = dpp->d_pad;
+    load_mod<LOGN>(&md, dpp, L + 1);
+    const u64 t = md.p;
+    const int8_t *qv = queries + (size_t)n * d;
+#pragma unroll 4
+    for (int u = 0; u < 32; u++) {
+        const u32 s = threadIdx.x + T * u, xx = s % dpad;
+        long v = xx < d ? (long)qv[xx] : 0;
+        sm[pidx(dpp->slot_pos[s])] = v < 0 ? (u64)(v + (long)t) : (u64)v;
+    }
+    ntt_inv<LOGN>(sm, md);
+#pragma unroll 8
+    for (int u = 0; u < 32; u++) {
+        const u32 e = threadIdx.x + T * u;
+        m_out[(size_t)n * N + e] = inv_finish(sm[pidx(e)], md);
+    }
+}
+
+// sm <- NTT(a) * NTT(s) brought back by INTT: the negacyclic product a*s mod p.
+// sv holds NTT(s) for the thread's 32 positions.
+template <int LOGN>
+__device__ __forceinline__ void poly_times_secret(u64 *sm, const u64 sv[32], const Mod &md)
+{
+    constexpr int T = (1 << LOGN) / 32;
+    ntt_fwd<LOGN>(sm, md);
+#pragma unroll
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        sm[pidx(e)] = mulmod(fwd_finish(sm[pidx(e)], md), sv[u], md);
+    }
+    ntt_inv<LOGN>(sm, md);
+}
+
+template <int LOGN>
+__device__ __forceinline__ void secret_ntt(u64 *sm, u64 sv[32], const int8_t *s, const Mod &md)
+{
+    constexpr int T = (1 << LOGN) / 32;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        const int v = s[e];
+        sm[pidx(e)] = v < 0 ? md.p - 1 : (u64)v;
+    }
+    ntt_fwd<LOGN>(sm, md);
+#pragma unroll
+    for (int u = 0; u < 32; u++) sv[u] = fwd_finish(sm[pidx(threadIdx.x + T * u)], md);
+    __syncthreads();
+}
+
+// CTA (client n, limb l): c1 = a, c0 = -a*s + e + Delta*m (reading R1).
+template <int LOGN>
+__global__ void NTT_LB_WIDE(LOGN) k_encrypt(const DevParams *dpp, const int8_t *secret, const u64 *m, const u64 *enc_a,
+                                       const int8_t *enc_e, u64 *cts)
+{
+    constexpr int N = 1 << LOGN, T = N / 32;
+    extern __shared__ u64 sm[];
+    __shared__ Mod md;
+    const u32 n = blockIdx.x;
+    const int l = blockIdx.y, L = dpp->L;
+    load_mod<LOGN>(&md, dpp, l);
+    const u64 q = md.p;
+    u64 sv[32];
+    secret_ntt<LOGN>(sm, sv, secret + (size_t)n * N, md);
+    const u64 *a = enc_a + ((size_t)n * L + l) * N;
+#pragma unroll 8
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        sm[pidx(e)] = a[e];
+    }
+    poly_times_secret<LOGN>(sm, sv, md);
+    u64 *c0 = cts + ((size_t)n * 2 * L + l) * N, *c1 = cts + ((size_t)n * 2 * L + L + l) * N;
+    const int8_t *ee = enc_e + (size_t)n * N;
+    const u64 *mm = m + (size_t)n * N;
+    const u64 dl = dpp->delta[l], dls = dpp->delta_s[l];
+#pragma unroll 4
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        const u64 as = inv_finish(sm[pidx(e)], md);
+        const int ev = ee[e];
+        u64 v = submod(ev < 0 ? q - (u64)(-ev) : (u64)ev, as, q);
+        v = addmod(v, csub(shoup_mul(mm[e], dl, dls, q), q), q);
+        c0[e] = v;
+        c1[e] = a[e];
+    }
+}
+
+// CTA (client n, modulus j, key kk * L + digit i): Galois key of element
+// k = (kk ? kg : k1), s' = sigma_k(s):
+//   b = -a*s + e + [i == j] P s'  (mod q_j),  b = -a*s + e (mod P).
+template <int LOGN>
+__global__ void NTT_LB_WIDE(LOGN) k_keygen(const DevParams *dpp, const int8_t *secret, const u64 *key_a,
+                                      const int8_t *key_e, u64 k1_inv, u64 kg_inv, u64 *keys)
+{
+    constexpr int N = 1 << LOGN, T = N / 32;
+    extern __shared__ u64 sm[];
+    __shared__ Mod md;
+    const u32 n = blockIdx.x;
+    const int j = blockIdx.y, L = dpp->L;
+    const int kk = blockIdx.z / L, i = blockIdx.z % L;
+    load_mod<LOGN>(&md, dpp, j);
+    const u64 p = md.p;
+    const int8_t *s = secret + (size_t)n * N;
+    u64 sv[32];
+    secret_ntt<LOGN>(sm, sv, s, md);
+    const u64 *a = key_a + ((((size_t)n * 2 + kk) * L + i) * (L + 1) + j) * N;
+#pragma unroll 8
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        sm[pidx(e)] = a[e];
+    }
+    poly_times_secret<LOGN>(sm, sv, md);
+    const int8_t *ee = key_e + (((size_t)n * 2 + kk) * L + i) * N;
+    u64 *kb = keys + (((((size_t)n * 2 + kk) * L + i) * 2 + 0) * (L + 1) + j) * N;
+    u64 *ka = keys + (((((size_t)n * 2 + kk) * L + i) * 2 + 1) * (L + 1) + j) * N;
+    const u64 kinv = kk ? kg_inv : k1_inv;
+    const u32 mask2n = 2 * N - 1;
+#pragma unroll 4
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        const u64 as = inv_finish(sm[pidx(e)], md);
+        const int ev = ee[e];
+        u64 v = submod(ev < 0 ? p - (u64)(-ev) : (u64)ev, as, p);
+        if (i == j) {
+            // s'[e]: the coefficient n0 = e * k^-1 mod 2N of s moves to X^e
+            // (sign + if n0 < N, else coefficient n0 - N with sign -).
+            const u32 n0 = (u32)(((u64)e * kinv) & mask2n);
+            int sp = n0 < (u32)N ? s[n0] : -s[n0 - N];
+            const u64 pm = dpp->pmodq[j];
+            if (sp > 0) v = addmod(v, pm, p);
+            else if (sp < 0) v = submod(v, pm, p);
+        }
+        kb[e] = v;
+        ka[e] = a[e];
+    }
+}
+
+// CTA (ciphertext n, limb l): x_l = [c0 + c1 s]_{q_l}, coefficient form.
+template <int LOGN>
+__global__ void NTT_LB_WIDE(LOGN) k_decrypt_residues(const DevParams *dpp, const int8_t *secret, const u32 *secret_index,
+                                                const u64 *cts, u64 *xs)
+{
+    constexpr int N = 1 << LOGN, T = N / 32;
+    extern __shared__ u64 sm[];
+    __shared__ Mod md;
+    const u32 n = blockIdx.x;
+    const int l = blockIdx.y, L = dpp->L;
+    load_mod<LOGN>(&md, dpp, l);
+    const u32 si = secret_index ? secret_index[n] : n;
+    u64 sv[32];
+    secret_ntt<LOGN>(sm, sv, secret + (size_t)si * N, md);
+    const u64 *c0 = cts + ((size_t)n * 2 * L + l) * N, *c1 = cts + ((size_t)n * 2 * L + L + l) * N;
+#pragma unroll 8
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        sm[pidx(e)] = c1[e];
+    }
+    poly_times_secret<LOGN>(sm, sv, md);
+    u64 *x = xs + ((size_t)n * L + l) * N;
+#pragma unroll 8
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        x[e] = addmod(inv_finish(sm[pidx(e)], md), c0[e], md.p);
+    }
+}
+
+// CTA (ciphertext n): m = round(t x / Q) mod t from the residues x_l, then
+// slot decoding (forward NTT mod t) and centring.  With y_l = x_l (Q/q_l)^-1
+// mod q_l, t x / Q = sum_l y_l t / q_l - (a multiple of t), so m is the
+// rounded sum of the integer parts and the 64-bit fractions of y_l t / q_l.
+template <int LOGN>
+__global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u64 *xs, int64_t *scores)
+{
+    constexpr int N = 1 << LOGN, T = N / 32;
+    extern __shared__ u64 sm[];
+    __shared__ Mod md;
+    const u32 n = blockIdx.x;
+    const int L = dpp->L;
+    load_mod<LOGN>(&md, dpp, L + 1);
+    const u64 t = md.p;
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        u64 ipart = 0;
+        unsigned __int128 frac = 0;
+        for (int l = 0; l < L; l++) {
+            const u64 q = dpp->m[l].p;
+            const u64 y = csub(shoup_mul(xs[((size_t)n * L + l) * N + e], dpp->theta[l], dpp->theta_s[l], q), q);
+            const unsigned __int128 num = (unsigned __int128)y * t;
+            const u64 quo = (u64)(num / q);
+            const u64 rem = (u64)(num - (unsigned __int128)quo * q);
+            ipart += quo;
+            frac += (u64)(((unsigned __int128)rem << 64) / q);
+        }
+        const u64 rnd = (u64)((frac + ((unsigned __int128)1 << 63)) >> 64);
+        sm[pidx(e)] = (ipart + rnd) % t;
+    }
+    ntt_fwd<LOGN>(sm, md);
+    for (int u = 0; u < 32; u++) {
+        const int s = threadIdx.x + T * u;
+        const u64 v = fwd_finish(sm[pidx(dpp->slot_pos[s])], md);
+        scores[(size_t)n * N + s] = v > t / 2 ? (int64_t)v - (int64_t)t : (int64_t)v;
+    }
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int LOGN>
+cudaError_t set_attrs_logn()
+{
+    const size_t sb = smem_words(1 << LOGN) * 8;
+    cudaError_t e = cudaSuccess;
+#define SA(k) if (e == cudaSuccess) e = set_smem(k<LOGN>, sb)
+    SA(k_encode_cluster);
+    SA(k_export_cluster);
+    SA(k_encode_query);
+    SA(k_encrypt);
+    SA(k_keygen);
+    SA(k_decrypt_residues);
+    SA(k_decrypt_scale);
+#undef SA
+    return e;
+}
+
+}  // namespace
+
+#define DISPATCH_LOGN(log_n, CALL)                  \
+    switch (log_n) {                                \
+    case 12: { constexpr int LG = 12; CALL; break; } \
+    case 13: { constexpr int LG = 13; CALL; break; } \
+    case 14: { constexpr int LG = 14; CALL; break; } \
+    default: return cudaErrorInvalidValue;          \
+    }
+
+static inline size_t smem_bytes(int log_n) { return smem_words(1 << log_n) * 8; }
+static inline int ntt_threads(int log_n) { return (1 << log_n) / 32; }
+
+static inline const DevParams *device_params_of(const DevParams &dp) { return dp.self; }
+
+cudaError_t set_client_kernel_attributes(int log_n)
+{
+    cudaError_t e;
+    DISPATCH_LOGN(log_n, e = set_attrs_logn<LG>());
+    return e;
+}
+
+cudaError_t launch_encode_clusters(const DevParams &dp, const EncodeArgs &a, cudaStream_t st)
+{
+    if (a.total_chunks == 0) return cudaSuccess;
+    const DevParams *dpp = device_params_of(dp);
+    dim3 grid(dp.g * dp.h, a.total_chunks);
+    DISPATCH_LOGN(dp.log_n, (k_encode_cluster<LG><<<grid, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_cluster(const DevParams &dp, const ClusterStore &cs, u32 cluster, u32 m, u64 *out,
+                                  cudaStream_t st)
+{
+    const DevParams *dpp = device_params_of(dp);
+    dim3 grid(dp.g * dp.h, dp.L, m);
+    DISPATCH_LOGN(dp.log_n, (k_export_cluster<LG><<<grid, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, cs, cluster,
+                                                                                                   out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_queries(const DevParams &dp, const int8_t *queries, u32 n, u64 *m_out, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const DevParams *dpp = device_params_of(dp);
+    DISPATCH_LOGN(dp.log_n, (k_encode_query<LG><<<n, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, queries, m_out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encrypt(const DevParams &dp, const int8_t *secret, const u64 *m, const u64 *enc_a,
+                           const int8_t *enc_e, u32 n, u64 *cts, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const DevParams *dpp = device_params_of(dp);
+    DISPATCH_LOGN(dp.log_n, (k_encrypt<LG><<<dim3(n, dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
+                                dpp, secret, m, enc_a, enc_e, cts)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keygen(const DevParams &dp, const int8_t *secret, const u64 *key_a, const int8_t *key_e, u32 n,
+                          u64, u64, u64 k1_inv, u64 kg_inv, u64 *keys, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const DevParams *dpp = device_params_of(dp);
+    DISPATCH_LOGN(dp.log_n, (k_keygen<LG><<<dim3(n, dp.L + 1, 2 * dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
+                                dpp, secret, key_a, key_e, k1_inv, kg_inv, keys)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decrypt(const DevParams &dp, const int8_t *secret, const u32 *secret_index, const u64 *cts, u32 n,
+                           u64 *xs, int64_t *scores, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const DevParams *dpp = device_params_of(dp);
+    DISPATCH_LOGN(dp.log_n, ({
+                      k_decrypt_residues<LG><<<dim3(n, dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
+                          dpp, secret, secret_index, cts, xs);
+                      k_decrypt_scale<LG><<<n, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, xs, scores);
+                  }));
+    return cudaGetLastError();
+}
+
+}  // namespace wally

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libwally (include/wally.h).
+
+Argument marshalling only: every call forwards torch tensors (device memory,
+or host memory for the ``_host`` variant) as raw pointers to the C ABI, where
+all of the computation runs in the library's CUDA kernels.  There is no CPU
+fallback: importing this module on a machine without the built library, or
+calling it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+WALLY_OK, WALLY_EINVAL, WALLY_ENOMEM, WALLY_ECUDA, WALLY_ETIMEOUT, WALLY_ESTATE = range(6)
+MAX_LIMBS = 8
+
+
+class WallyError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"wally error {code}: {msg}")
+        self.code = code
+
+
+class wally_params(ctypes.Structure):
+    _fields_ = [
+        ("log_n", ctypes.c_uint32), ("num_q", ctypes.c_uint32), ("q_bits", ctypes.c_uint32),
+        ("t_bits", ctypes.c_uint32), ("dim", ctypes.c_uint32), ("device", ctypes.c_int32),
+        ("q", ctypes.POINTER(ctypes.c_uint64)), ("p_special", ctypes.c_uint64), ("t", ctypes.c_uint64),
+        ("max_wave", ctypes.c_uint32),
+    ]
+
+
+class wally_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint32), ("log_n", ctypes.c_uint32), ("num_q", ctypes.c_uint32), ("dim", ctypes.c_uint32),
+        ("d_pad", ctypes.c_uint32), ("g", ctypes.c_uint32), ("h", ctypes.c_uint32),
+        ("num_clusters", ctypes.c_uint32), ("q", ctypes.c_uint64 * MAX_LIMBS),
+        ("p_special", ctypes.c_uint64), ("t", ctypes.c_uint64), ("zeta_t", ctypes.c_uint64),
+        ("k1", ctypes.c_uint64), ("kg", ctypes.c_uint64), ("ct_words", ctypes.c_uint64),
+        ("keys_words", ctypes.c_uint64), ("total_chunks", ctypes.c_uint64), ("cluster_bytes", ctypes.c_uint64),
+        ("max_wave", ctypes.c_uint32),
+    ]
+
+
+_vp = ctypes.c_void_p
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+
+# name -> (restype, argtypes): the full C ABI of include/wally.h
+SIGNATURES = {
+    "wally_setup_params": (ctypes.c_int, [ctypes.POINTER(wally_params), ctypes.POINTER(_vp)]),
+    "wally_destroy": (None, [_vp]),
+    "wally_query_info": (ctypes.c_int, [_vp, ctypes.POINTER(wally_info)]),
+    "wally_load_clusters": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp]),
+    "wally_cluster_chunks": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(_u32)]),
+    "wally_export_cluster": (ctypes.c_int, [_vp, _u32, _vp, _vp]),
+    "wally_eval_batch": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "wally_eval_batch_host": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "wally_rotate": (ctypes.c_int, [_vp, _u32, _u64, _vp, _vp, _vp, _vp]),
+    "wally_sync": (ctypes.c_int, [_vp, _vp]),
+    "wally_keygen": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
+    "wally_encrypt_query": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "wally_decrypt_scores": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
+    "wally_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libwally.so (optionally building it first).  Raises if absent."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libwally.so is not built ({path}); run __graft_entry__.build()")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != WALLY_OK:
+        raise WallyError(rc, load().wally_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to libwally must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("this call takes device tensors")
+
+
+def _u64_view(t: torch.Tensor) -> torch.Tensor:
+    """uint64 residues are carried in int64 tensors (same bits)."""
+    return t
+
+
+# ------------------------------------------------------------------ same names as the C ABI
+
+def wally_setup_params(log_n: int, num_q: int, q_bits: int, t_bits: int, dim: int, device: int = 0,
+                       q=None, p_special: int = 0, t: int = 0, max_wave: int = 0) -> int:
+    lib = load()
+    prm = wally_params(log_n, num_q, q_bits, t_bits, dim, device, None, p_special, t, max_wave)
+    qarr = None
+    if q is not None:
+        qarr = (ctypes.c_uint64 * len(q))(*q)
+        prm.q = ctypes.cast(qarr, ctypes.POINTER(ctypes.c_uint64))
+    out = _vp()
+    _check(lib.wally_setup_params(ctypes.byref(prm), ctypes.byref(out)))
+    return out.value
+
+
+def wally_destroy(ctx: int) -> None:
+    load().wally_destroy(ctx)
+
+
+def wally_query_info(ctx: int) -> wally_info:
+    info = wally_info()
+    _check(load().wally_query_info(ctx, ctypes.byref(info)))
+    return info
+
+
+def wally_load_clusters(ctx: int, sizes, embeddings, stream=None) -> None:
+    """sizes: uint32 numpy array [K]; embeddings: int8 numpy array [sum sizes][dim] (host)."""
+    import numpy as np
+    sizes = np.ascontiguousarray(sizes, dtype=np.uint32)
+    emb = np.ascontiguousarray(embeddings, dtype=np.int8)
+    _check(load().wally_load_clusters(ctx, len(sizes), sizes.ctypes.data, emb.ctypes.data if emb.size else None,
+                                      _stream(stream)))
+
+
+def wally_cluster_chunks(ctx: int, cluster_id: int) -> int:
+    m = _u32()
+    _check(load().wally_cluster_chunks(ctx, cluster_id, ctypes.byref(m)))
+    return m.value
+
+
+def wally_export_cluster(ctx: int, cluster_id: int, out: torch.Tensor, stream=None) -> None:
+    _require_cuda(out)
+    _check(load().wally_export_cluster(ctx, cluster_id, _ptr(out), _stream(stream)))
+
+
+def wally_eval_batch(ctx: int, n: int, cluster_ids, cts, galois_keys, input_index, out_offsets, out,
+                     stream=None) -> None:
+    _require_cuda(cluster_ids, cts, galois_keys, input_index, out_offsets, out)
+    _check(load().wally_eval_batch(ctx, n, _ptr(cluster_ids), _ptr(cts), _ptr(galois_keys), _ptr(input_index),
+                                   _ptr(out_offsets), _ptr(out), _stream(stream)))
+
+
+def wally_eval_batch_host(ctx: int, n: int, cluster_ids, cts, galois_keys, input_index, out_offsets, out,
+                          stream=None) -> None:
+    """Host tensors (pinned for asynchronous copies); returns when out is filled."""
+    for t in (cluster_ids, cts, galois_keys, input_index, out_offsets, out):
+        if t is not None and t.is_cuda:
+            raise ValueError("wally_eval_batch_host takes host tensors")
+    _check(load().wally_eval_batch_host(ctx, n, _ptr(cluster_ids), _ptr(cts), _ptr(galois_keys),
+                                        _ptr(input_index), _ptr(out_offsets), _ptr(out), _stream(stream)))
+
+
+def wally_rotate(ctx: int, n: int, galois_elt: int, cts, keys, out, stream=None) -> None:
+    _require_cuda(cts, keys, out)
+    _check(load().wally_rotate(ctx, n, galois_elt, _ptr(cts), _ptr(keys), _ptr(out), _stream(stream)))
+
+
+def wally_sync(ctx: int, stream=None) -> None:
+    _check(load().wally_sync(ctx, _stream(stream)))
+
+
+def wally_keygen(ctx: int, n: int, secret, key_a, key_e, galois_keys, stream=None) -> None:
+    _require_cuda(secret, key_a, key_e, galois_keys)
+    _check(load().wally_keygen(ctx, n, _ptr(secret), _ptr(key_a), _ptr(key_e), _ptr(galois_keys), _stream(stream)))
+
+
+def wally_encrypt_query(ctx: int, n: int, secret, queries, enc_a, enc_e, cts, stream=None) -> None:
+    _require_cuda(secret, queries, enc_a, enc_e, cts)
+    _check(load().wally_encrypt_query(ctx, n, _ptr(secret), _ptr(queries), _ptr(enc_a), _ptr(enc_e), _ptr(cts),
+                                      _stream(stream)))
+
+
+def wally_decrypt_scores(ctx: int, n: int, secret, secret_index, cts, scores, stream=None) -> None:
+    _require_cuda(secret, secret_index, cts, scores)
+    _check(load().wally_decrypt_scores(ctx, n, _ptr(secret), _ptr(secret_index), _ptr(cts), _ptr(scores),
+                                       _stream(stream)))
+
+
+def wally_last_error() -> str:
+    return load().wally_last_error().decode()
+
+
+# ------------------------------------------------------------------ convenience
+
+def u64_tensor(a, device) -> torch.Tensor:
+    """numpy uint64 array -> int64 tensor with the same bits, on `device`."""
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)
+
+
+def to_u64_numpy(t: torch.Tensor):
+    import numpy as np
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+class Context:
+    """Owns one wally_ctx; a convenience wrapper around the functions above."""
+
+    def __init__(self, log_n, num_q, q_bits, t_bits, dim, device=0, max_wave=0, **kw):
+        self.ptr = wally_setup_params(log_n, num_q, q_bits, t_bits, dim, device=device, max_wave=max_wave, **kw)
+        self.info = wally_query_info(self.ptr)
+        self.device = torch.device("cuda", device)
+
+    @property
+    def N(self):
+        return self.info.n
+
+    @property
+    def L(self):
+        return self.info.num_q
+
+    @property
+    def q(self):
+        return [int(self.info.q[i]) for i in range(self.L)]
+
+    @property
+    def P(self):
+        return int(self.info.p_special)
+
+    def refresh(self):
+        self.info = wally_query_info(self.ptr)
+
+    def close(self):
+        if self.ptr:
+            wally_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 Wally server path.
+
+One step = one whole batch of the workload (default: the full-scale batch,
+3.2M x 192 database in 1,800 clusters, 500,000 real queries plus the
+negative-binomial fakes of every client) evaluated end to end on the device:
+grouping by cluster, inputs to NTT form, g-1 baby-step rotations, the grouped
+plaintext x ciphertext products, h-1 giant-step rotations, outputs to
+coefficient form.  Inputs are resident in HBM when the timed region starts
+(they are far larger than L2: a 2,048-client pool of submissions and the
+~91 GB encoded database).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank evaluates its own copy of the batch (independent
+replicas; weak scaling; the only collectives are the timing barrier and the
+max-over-ranks of the step time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted similarity QPS @3.2M×192, 500k batch, 1 GB300 (bit-exact); p50/p99 latency"
+
+
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines: list[str] = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic work
+
+def modmuls_per_kind(L: int, N: int, log_n: int, ks_count: int, mac_pairs: int, g: int, h: int) -> dict:
+    """64-bit modular multiplications the method performs, per kernel kind,
+    for `ks_count` key switches and `mac_pairs` (query, chunk) products: an
+    NTT of N points is N/2 log2 N butterflies (one product each) plus N for the
+    inverse's N^-1; a key switch is L inverse NTTs (digits), L^2 NTTs (digits
+    into the other moduli) + 2(L+1)L key products + 2 inverse NTTs (ModDown
+    residue mod P), then 2L NTTs + 2LN P^-1 products; a (query, chunk)
+    product is g*h*2*L*N multiply-accumulates."""
+    ntt = N // 2 * log_n
+    return {
+        "ks_a": ks_count * L * (ntt + N),
+        "ks_b": ks_count * ((L * L) * ntt + 2 * (ntt + N) + 2 * (L + 1) * L * N),
+        "ks_c": ks_count * (2 * L * ntt + 2 * L * N),
+        "mac": mac_pairs * g * h * 2 * L * N,
+    }
+
+
+# ---------------------------------------------------------------- the oracle arm
+
+def oracle_sample_qps(workload: str, seconds: float, seed: int = 0) -> dict:
+    """Time the CPU oracle on a bounded sample of the workload's queries, on
+    every host core.  Returns {value, unit, cores, sample, kind}."""
+    import numpy as np
+    import oracle as O
+    from paper_2406_06761_gb300 import workload as W
+    w = W.WORKLOADS[workload]
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    cores = os.cpu_count() or 1
+    sizes = W.cluster_sizes(w, seed)
+    ids, is_real = W.query_mix(w, sizes, seed)
+    # one single-thread probe to size the sample to about `seconds`
+    c0 = int(ids[0])
+    rows = np.cumsum(sizes) - sizes
+    emb = W.embeddings(int(sizes.sum()), w.dim, w.entry_bound, seed)
+    m0, pt0 = O.encode_cluster(prm, emb[rows[c0]:rows[c0] + sizes[c0]])
+    cl = [(m0, O.ptxt_to_ntt(prm, m0, pt0))]
+    n_probe = 1
+    cr = W.client_randomness(cores, prm.N, prm.q, prm.P, seed, index=999)
+    qv = W.query_vectors(cores, w.dim, w.entry_bound, seed, index=999)
+    keys = np.stack([O.keygen_pair(prm, cr.secret[i], cr.key_a[i], cr.key_e[i]) for i in range(cores)])
+    cts = np.stack([O.encrypt_query(prm, cr.secret[i], qv[i], cr.enc_a[i], cr.enc_e[i]) for i in range(cores)])
+    t0 = time.perf_counter()
+    O.eval_batch(prm, cl, np.zeros(n_probe, np.uint32), cts[:n_probe], keys[:n_probe], nthreads=1)
+    single = time.perf_counter() - t0
+    per_round = single * 1.15  # all cores busy: a little slower per query
+    rounds = max(1, int(seconds / per_round))
+    n = rounds * cores
+    sel = np.arange(n) % cores
+    t0 = time.perf_counter()
+    O.eval_batch(prm, cl, np.zeros(n, np.uint32), cts[sel], keys[sel], nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} queries of the {workload} workload (N={prm.N}, L={prm.L}, one {m0}-chunk cluster), "
+                      f"{cores} threads, {dt:.1f} s; single-thread latency {single * 1e3:.0f} ms/query",
+            "single_thread_ms": single * 1e3}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    k, w = args.steps, args.warmup
+    per_step = max(5.0, min(60.0, 150.0 / max(1, k + w)))
+    vals = []
+    res = None
+    for i in range(w + k):
+        res = oracle_sample_qps(args.workload, per_step)
+        if i >= w:
+            vals.append(res["value"])
+    v = statistics.mean(vals)
+    line = {"metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": args.gpus, "steps": k, "warmup": w,
+            "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "note": "CPU oracle on a bounded sample per step"},
+            "cpu_baseline": {"value": v, "unit": "queries/s", "kind": "oracle", "cores": res["cores"],
+                             "sample": res["sample"]},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="full_scale")
+    ap.add_argument("--pool", type=int, default=2048)
+    ap.add_argument("--max-wave", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--real-queries", type=int, default=None, help="override the batch size (testing)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_06761_gb300 import harness as H
+    from paper_2406_06761_gb300 import wally as Wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    Wl.load()
+    peaks = Wl.wally_measure_int_peaks(local)
+    log("integer peaks", {k: f"{v:.3e}" for k, v in peaks.items()})
+
+    t_setup = time.perf_counter()
+    wl = H.DeviceWorkload(args.workload, device=local, pool=args.pool, max_wave=args.max_wave,
+                          real_queries=args.real_queries, keep_embeddings=False, verbose=(rank == 0))
+    info = wl.ctx.info
+    n = wl.n
+    n_real = int(wl.is_real.sum())
+    # allocate the evaluation workspace with one tiny call, then size the output buffer
+    b0 = wl.device_batch(0, 1)
+    tmp = wl.alloc_out(b0[3])
+    wl.eval(b0, tmp)
+    Wl.wally_sync(wl.ctx.ptr)
+    del tmp
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info(dev)
+    total_chunks = int(wl.chunks[wl.ids].sum())
+    out_bytes_all = total_chunks * wl.ctw * 8
+    budget = int(free * 0.85) - (2 << 30)
+    subs = wl.sub_batches(None if out_bytes_all <= budget else budget)
+    batches = [wl.device_batch(lo, hi) for lo, hi in subs]
+    max_chunks = max(b[3] for b in batches)
+    out = wl.alloc_out(max_chunks)
+    setup_s = time.perf_counter() - t_setup
+    log(f"setup {setup_s:.1f}s: {n} queries ({n_real} real), {len(wl.sizes)} clusters, "
+        f"{info.total_chunks} chunks ({info.cluster_bytes / 1e9:.1f} GB), {len(subs)} sub-batch(es), "
+        f"output buffer {max_chunks * wl.ctw * 8 / 1e9:.1f} GB")
+
+    stream = torch.cuda.current_stream(dev)
+
+    def step(record=None):
+        for b in batches:
+            wl.eval(b, out[:b[3]], stream)
+            if record is not None:
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(stream)
+                record.append((ev, b[0].numel()))
+
+    for i in range(args.warmup):
+        t0 = time.perf_counter()
+        step()
+        Wl.wally_sync(wl.ctx.ptr)
+        log(f"warm-up {i}: {time.perf_counter() - t0:.2f}s")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    Wl.wally_profile_enable(wl.ctx.ptr, True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    marks = []
+    start.record(stream)
+    for _ in range(args.steps):
+        step(marks)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    Wl.wally_sync(wl.ctx.ptr)
+    ms_total = start.elapsed_time(end)
+    prof = Wl.wally_profile_read(wl.ctx.ptr)
+    Wl.wally_profile_enable(wl.ctx.ptr, False)
+    clk = clocks.stop()
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n / (ms_step / 1e3)
+
+    # latency: completion time of each query's sub-batch within its step
+    lat = []
+    for ev, cnt in marks[:len(batches)]:
+        lat += [start.elapsed_time(ev)] * cnt
+    lat = np.array(lat)
+    p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+
+    # roofline of the dominant kernel
+    g, h, L, N = info.g, info.h, info.num_q, info.n
+    pairs = int(wl.chunks[wl.ids].sum())
+    ks_count = args.steps * (n * (g - 1) + pairs * (h - 1))
+    work = modmuls_per_kind(L, N, info.log_n, ks_count, args.steps * pairs, g, h)
+    kern = {}
+    for kind, (launches, tms) in prof.items():
+        kern[kind] = {"launches": launches, "total_ms": tms, "share": tms / max(1e-9, sum(v[1] for v in prof.values()))}
+    dom = max(kern, key=lambda k: kern[k]["total_ms"])
+    roof = None
+    if dom in work:
+        achieved = work[dom] / (kern[dom]["total_ms"] / 1e3)
+        peak = peaks["mac128_per_s"] if dom == "mac" else peaks["butterfly_per_s"]
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
+                "unit": "Gmodmul/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured: wally_measure_int_peaks (" +
+                               ("128-bit multiply-accumulate" if dom == "mac" else "NTT butterfly") +
+                               " throughput, all SMs, this GPU)",
+                "avg_launch_ms": kern[dom]["total_ms"] / kern[dom]["launches"]}
+    alg_bytes_q = 8 * (wl.ctw + wl.keysw + wl.ctw * float(wl.chunks[wl.ids].mean()))
+    hbm_ctx = {"algorithmic_bytes_per_query": alg_bytes_q,
+               "achieved_GBps": value / world * alg_bytes_q / 1e9,
+               "peak_GBps": 6790.0, "frac_of_measured_hbm": value / world * alg_bytes_q / 1e9 / 6790.0}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(wl, subs, args, dev)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu = oracle_sample_qps(args.workload, args.cpu_seconds)
+        except Exception as ex:  # the oracle is optional on the GPU machine
+            cpu = {"value": None, "error": str(ex)[:200]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "queries": n, "real_queries": n_real, "clusters": int(len(wl.sizes)),
+                   "embeddings": int(wl.sizes.sum()), "N": N, "L": L, "d": info.dim, "g": g, "h": h,
+                   "client_pool": wl.pool_size, "sub_batches": len(subs), "max_wave": int(info.max_wave),
+                   "l2": "inputs larger than L2 (91 GB database, client pool > 129 MB); no flush"},
+        "real_qps": world * n_real / (ms_step / 1e3),
+        "latency_ms": {"p50": p50, "p99": p99, "note": "completion time of the query's sub-batch within a step"},
+        "gpu_launches": int(sum(v[0] for v in prof.values()) / args.steps),
+        "roofline": roof,
+        "kernels": kern,
+        "hbm_context": hbm_ctx,
+        "int_peaks": peaks,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(wl, subs, args, dev):
+    """Same metric through wally_eval_batch_host: the host holds the client
+    pool (pinned) and receives every output; each query's ciphertext and keys
+    are copied to the device and its score ciphertexts back, inside the timed
+    region.  Outputs land in a reused pinned host buffer of one call."""
+    import numpy as np
+    import torch
+    from paper_2406_06761_gb300 import wally as Wl
+    cts_h = wl.pool.cts.cpu().pin_memory()
+    keys_h = wl.pool.keys.cpu().pin_memory()
+    # calls of at most ~6 GB of outputs each
+    cap_q = max(1, int(6e9 // (8 * wl.ctw * max(1, int(wl.chunks.max())))))
+    calls = []
+    for lo, hi in subs:
+        for a in range(lo, hi, cap_q):
+            calls.append((a, min(hi, a + cap_q)))
+    prepared = []
+    max_chunks = 0
+    for lo, hi in calls:
+        ids = wl.ids[lo:hi]
+        m = wl.chunks[ids]
+        offs = np.concatenate([[0], np.cumsum(m)[:-1]]).astype(np.int64)
+        max_chunks = max(max_chunks, int(m.sum()))
+        prepared.append((torch.from_numpy(ids.astype(np.int32)).pin_memory(),
+                         torch.from_numpy(wl.input_index[lo:hi].astype(np.int32)).pin_memory(),
+                         torch.from_numpy(offs).pin_memory(), int(m.sum())))
+    out_h = torch.empty((max_chunks, 2, wl.L, wl.N), dtype=torch.int64).pin_memory()
+    h2d = d2h = 0
+    for ids, idx, offs, ch in prepared:
+        h2d += ids.numel() * 8 * (wl.ctw + wl.keysw) + ids.numel() * 16
+        d2h += ch * wl.ctw * 8
+
+    def one():
+        for ids, idx, offs, ch in prepared:
+            Wl.wally_eval_batch_host(wl.ctx.ptr, ids.numel(), ids, cts_h, keys_h, idx, offs, out_h[:ch])
+    one()  # warm-up (pins, staging buffers)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    one()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    return {"value": wl.n / dt, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "calls": len(prepared), "seconds": dt}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

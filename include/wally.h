@@ -161,6 +161,30 @@ int wally_rotate(wally_ctx *ctx, uint32_t n, uint64_t galois_elt, const uint64_t
  * the previous wally_sync (and clear it). */
 int wally_sync(wally_ctx *ctx, void *stream);
 
+/* ---------------------------------------------------------------- measurement
+ * Per-launch device time of the evaluation kernels, taken with CUDA events
+ * recorded on the launch stream around every launch (observability; the
+ * paper has no counterpart).  wally_profile_enable(ctx, 1) starts a fresh
+ * collection, 0 stops it.  wally_profile_read synchronises the device, sums
+ * launches and milliseconds per kernel kind into out[0 .. *count) (at most
+ * cap entries) and clears the collection. */
+typedef struct {
+    char name[16];       /* to_ntt, ks_a, ks_b, ks_c, mac, output, plan */
+    uint64_t launches;
+    double total_ms;
+} wally_kernel_time;
+
+int wally_profile_enable(wally_ctx *ctx, int enable);
+int wally_profile_read(wally_ctx *ctx, wally_kernel_time *out, uint32_t cap, uint32_t *count);
+
+/* Throughput ceiling of the integer primitives on `device` (all SMs busy,
+ * independent operations, no memory traffic): 64-bit Shoup modular
+ * multiplications, NTT butterflies (one Shoup product plus three
+ * additions/comparisons), and 64x64 -> 128-bit multiply-accumulates, each in
+ * operations per second.  Used as the denominator of the integer-ALU
+ * roofline.  Synchronous; allocates a few kilobytes. */
+int wally_measure_int_peaks(int32_t device, double *modmul_per_s, double *butterfly_per_s, double *mac128_per_s);
+
 /* ---------------------------------------------------------------- client side
  * Sec. 2 and Alg. "Client Query Generation".  The random numbers a client
  * draws are inputs, so that results are reproducible:

@@ -385,4 +385,4 @@ def eval_batch(prm: Params, clusters_ntt: list, ids, cts, keys, nthreads: int | 
                                nthreads or os.cpu_count() or 1)
     if rc != 0:
         raise ValueError("or_eval_batch rejected the input")
-    return out, offs
+    return out, offs.astype(np.int64)

@@ -73,6 +73,47 @@ struct DevBuf {
     }
 };
 
+// Per-launch CUDA events, summed per kernel kind when read.
+struct EventProfiler : Profiler {
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    cudaEvent_t open_[KK_COUNT] = {};
+    cudaEvent_t take()
+    {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void begin(int kind, cudaStream_t st) override
+    {
+        open_[kind] = take();
+        cudaEventRecord(open_[kind], st);
+    }
+    void end(int kind, cudaStream_t st) override
+    {
+        cudaEvent_t e = take();
+        cudaEventRecord(e, st);
+        recs.push_back({kind, open_[kind], e});
+    }
+    void reset()
+    {
+        used = 0;
+        recs.clear();
+    }
+    ~EventProfiler()
+    {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
+
 }  // namespace
 
 struct wally_ctx {
@@ -109,6 +150,10 @@ struct wally_ctx {
     DevBuf<void *> stage_ptrs[2];
     // client temporaries
     DevBuf<u64> tmp;
+    // optional per-launch timing
+    bool prof_on = false;
+    EventProfiler prof;
+    Profiler *pr() { return prof_on ? &prof : nullptr; }
 
     size_t ctw() const { return (size_t)2 * L * N; }
     size_t keysw() const { return (size_t)2 * L * 2 * (L + 1) * N; }
@@ -285,12 +330,12 @@ int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t s
     const DevParams &dp = c->dp;
     const size_t ctw = c->ctw(), keysw = c->keysw();
     const uint32_t L = c->L, g = c->g, h = c->h;
-    CUDA_TRY(launch_wave_plan(wp, c->d_chunks.p, wave_len, st));
+    CUDA_TRY(launch_wave_plan(wp, c->d_chunks.p, wave_len, st, c->pr()));
     // a1: ciphertexts into slot 0 of the baby-step array, keys (Montgomery)
     CUDA_TRY(launch_to_ntt(dp, wp.src_ct, nullptr, 0, c->ctp.p, (size_t)g * ctw, 2 * L, L, wave_len, wp.counts,
-                           false, st));
+                           false, st, c->pr()));
     CUDA_TRY(launch_to_ntt(dp, wp.src_key, nullptr, 0, c->keysN.p, keysw, 4 * L * (L + 1), L + 1, wave_len,
-                           wp.counts, true, st));
+                           wp.counts, true, st, c->pr()));
     // a2: ct'[j] = Rot_1(ct'[j-1])
     for (uint32_t j = 1; j < g; j++) {
         RotArgs a = rot_args(c);
@@ -303,10 +348,10 @@ int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t s
         a.n_max = wave_len;
         a.n_dev = wp.counts;
         a.galois = c->k1;
-        CUDA_TRY(launch_rotate(dp, a, st));
+        CUDA_TRY(launch_rotate(dp, a, st, c->pr()));
     }
     // a3: T_i = sum_b P'_{k,i,b} ct'[b]
-    CUDA_TRY(launch_mac(dp, cluster_store(c), wp, c->ctp.p, c->T.p, wave_len, c->m_max, c->num_sms, st));
+    CUDA_TRY(launch_mac(dp, cluster_store(c), wp, c->ctp.p, c->T.p, wave_len, c->m_max, c->num_sms, st, c->pr()));
     // a4: S = T_{h-1}; S = Rot_g(S) + T_i, i = h-2 .. 0
     const uint32_t np_max = wave_len * c->m_max;
     for (int i = (int)h - 2; i >= 0; i--) {
@@ -328,11 +373,11 @@ int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t s
         a.n_max = np_max;
         a.n_dev = wp.counts + 1;
         a.galois = c->kg;
-        CUDA_TRY(launch_rotate(dp, a, st));
+        CUDA_TRY(launch_rotate(dp, a, st, c->pr()));
     }
     // a5: back to coefficient form, into the caller's output
-    if (h == 1) CUDA_TRY(launch_output(dp, wp, c->T.p, ctw, np_max, st));
-    else CUDA_TRY(launch_output(dp, wp, c->S.p, ctw, np_max, st));
+    if (h == 1) CUDA_TRY(launch_output(dp, wp, c->T.p, ctw, np_max, st, c->pr()));
+    else CUDA_TRY(launch_output(dp, wp, c->S.p, ctw, np_max, st, c->pr()));
     return WALLY_OK;
 }
 
@@ -768,6 +813,46 @@ int wally_sync(wally_ctx *c, void *stream)
         CUDA_TRY(cudaMemset(c->d_err, 0, 4));
         return fail(WALLY_EINVAL, "a query named a cluster id out of range");
     }
+    return WALLY_OK;
+}
+
+int wally_profile_enable(wally_ctx *c, int enable)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    DeviceGuard guard(c->device);
+    cudaDeviceSynchronize();
+    c->prof.reset();
+    c->prof_on = enable != 0;
+    return WALLY_OK;
+}
+
+int wally_profile_read(wally_ctx *c, wally_kernel_time *out, uint32_t cap, uint32_t *count)
+{
+    static const char *names[KK_COUNT] = {"to_ntt", "ks_a", "ks_b", "ks_c", "mac", "output", "plan"};
+    if (!c || !count) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    double ms[KK_COUNT] = {};
+    uint64_t launches[KK_COUNT] = {};
+    for (auto &r : c->prof.recs) {
+        float t = 0;
+        CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.kind] += t;
+        launches[r.kind]++;
+    }
+    c->prof.reset();
+    uint32_t n = 0;
+    for (int k = 0; k < KK_COUNT; k++) {
+        if (!launches[k]) continue;
+        if (out && n < cap) {
+            memset(&out[n], 0, sizeof(out[n]));
+            strncpy(out[n].name, names[k], sizeof(out[n].name) - 1);
+            out[n].launches = launches[k];
+            out[n].total_ms = ms[k];
+        }
+        n++;
+    }
+    *count = n;
     return WALLY_OK;
 }
 

@@ -507,13 +507,28 @@ cudaError_t set_kernel_attributes(int log_n, u32 g)
 // The parameter block is read from device memory by every kernel.
 static inline const DevParams *device_params_of(const DevParams &dp) { return dp.self; }
 
+struct ProfScope {
+    Profiler *pr;
+    int kind;
+    cudaStream_t st;
+    ProfScope(Profiler *p, int k, cudaStream_t s) : pr(p), kind(k), st(s)
+    {
+        if (pr) pr->begin(kind, st);
+    }
+    ~ProfScope()
+    {
+        if (pr) pr->end(kind, st);
+    }
+};
+
 cudaError_t launch_to_ntt(const DevParams &dp, const u64 *const *src_ptrs, const u64 *src, size_t src_stride,
                           u64 *dst, size_t dst_stride, u32 polys, u32 mod_cycle, u32 n_max, const u32 *n_dev,
-                          bool mont, cudaStream_t st)
+                          bool mont, cudaStream_t st, Profiler *pr)
 {
     if (n_max == 0) return cudaSuccess;
     const DevParams *dpp = device_params_of(dp);
     dim3 grid(n_max, polys);
+    ProfScope ps(pr, KK_TO_NTT, st);
     DISPATCH_LOGN(dp.log_n, (k_to_ntt<LG><<<grid, ntt_threads(LG), smem_bytes(LG), st>>>(
                                 dpp, src_ptrs, src, src_stride, dst, dst_stride, mod_cycle, n_max, n_dev, mont)));
     return cudaGetLastError();
@@ -530,21 +545,30 @@ cudaError_t launch_from_ntt(const DevParams &dp, const u64 *src, u64 *dst, u32 p
     return cudaGetLastError();
 }
 
-cudaError_t launch_rotate(const DevParams &dp, const RotArgs &a, cudaStream_t st)
+cudaError_t launch_rotate(const DevParams &dp, const RotArgs &a, cudaStream_t st, Profiler *pr)
 {
     if (a.n_max == 0) return cudaSuccess;
     const DevParams *dpp = device_params_of(dp);
     const int L = dp.L;
     DISPATCH_LOGN(dp.log_n, ({
-                      k_ks_a<LG><<<dim3(a.n_max, L), ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a);
-                      k_ks_b<LG><<<dim3(a.n_max, L + 1), ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a);
-                      k_ks_c<LG><<<dim3(a.n_max, L), ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a);
+                      {
+                          ProfScope ps(pr, KK_KS_A, st);
+                          k_ks_a<LG><<<dim3(a.n_max, L), ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a);
+                      }
+                      {
+                          ProfScope ps(pr, KK_KS_B, st);
+                          k_ks_b<LG><<<dim3(a.n_max, L + 1), ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a);
+                      }
+                      {
+                          ProfScope ps(pr, KK_KS_C, st);
+                          k_ks_c<LG><<<dim3(a.n_max, L), ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a);
+                      }
                   }));
     return cudaGetLastError();
 }
 
 cudaError_t launch_mac(const DevParams &dp, const ClusterStore &cs, const WavePlan &wp, const u64 *ctp, u64 *T,
-                       u32 max_wave, u32 m_max, int num_sms, cudaStream_t st)
+                       u32 max_wave, u32 m_max, int num_sms, cudaStream_t st, Profiler *pr)
 {
     const DevParams *dpp = device_params_of(dp);
     const size_t smem = (size_t)dp.d_pad * cs.ts * 8;
@@ -554,6 +578,7 @@ cudaError_t launch_mac(const DevParams &dp, const ClusterStore &cs, const WavePl
     u64 grid = (u64)num_sms * 3;
     if (grid > items) grid = items;
     if (grid == 0) return cudaSuccess;
+    ProfScope ps(pr, KK_MAC, st);
     switch (dp.g) {
     case 4: k_mac<4, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max); break;
     case 8: k_mac<8, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max); break;
@@ -565,10 +590,11 @@ cudaError_t launch_mac(const DevParams &dp, const ClusterStore &cs, const WavePl
 }
 
 cudaError_t launch_output(const DevParams &dp, const WavePlan &wp, const u64 *S, size_t S_stride, u32 n_max,
-                          cudaStream_t st)
+                          cudaStream_t st, Profiler *pr)
 {
     if (n_max == 0) return cudaSuccess;
     const DevParams *dpp = device_params_of(dp);
+    ProfScope ps(pr, KK_OUTPUT, st);
     DISPATCH_LOGN(dp.log_n, (k_output<LG><<<dim3(n_max, 2 * dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
                                 dpp, wp, S, S_stride, n_max)));
     return cudaGetLastError();
@@ -599,8 +625,9 @@ cudaError_t launch_gather_wave(const WavePlan &wp, const u32 *sorted_q, const u3
     return cudaGetLastError();
 }
 
-cudaError_t launch_wave_plan(const WavePlan &wp, const u32 *cluster_chunks, u32, cudaStream_t st)
+cudaError_t launch_wave_plan(const WavePlan &wp, const u32 *cluster_chunks, u32, cudaStream_t st, Profiler *pr)
 {
+    ProfScope ps(pr, KK_PLAN, st);
     k_wave_plan<<<1, 1024, 0, st>>>(wp, cluster_chunks);
     return cudaGetLastError();
 }

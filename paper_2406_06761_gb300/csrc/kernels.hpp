@@ -54,17 +54,25 @@ struct ClusterStore {
     u32 ts;
 };
 
+// Optional timing of every launch with CUDA events on the launch stream.
+enum KernelKind { KK_TO_NTT = 0, KK_KS_A, KK_KS_B, KK_KS_C, KK_MAC, KK_OUTPUT, KK_PLAN, KK_COUNT };
+struct Profiler {
+    virtual void begin(int kind, cudaStream_t st) = 0;
+    virtual void end(int kind, cudaStream_t st) = 0;
+    virtual ~Profiler() {}
+};
+
 cudaError_t set_kernel_attributes(int log_n, u32 g);
 
 cudaError_t launch_to_ntt(const DevParams &dp, const u64 *const *src_ptrs, const u64 *src, size_t src_stride,
                           u64 *dst, size_t dst_stride, u32 polys, u32 mod_cycle, u32 n_max, const u32 *n_dev,
-                          bool mont, cudaStream_t st);
-cudaError_t launch_rotate(const DevParams &dp, const RotArgs &a, cudaStream_t st);
+                          bool mont, cudaStream_t st, Profiler *pr = nullptr);
+cudaError_t launch_rotate(const DevParams &dp, const RotArgs &a, cudaStream_t st, Profiler *pr = nullptr);
 cudaError_t launch_mac(const DevParams &dp, const ClusterStore &cs, const WavePlan &wp, const u64 *ctp, u64 *T,
-                       u32 max_wave, u32 m_max, int num_sms, cudaStream_t st);
+                       u32 max_wave, u32 m_max, int num_sms, cudaStream_t st, Profiler *pr = nullptr);
 // Output: pair p (INTT of S + p*S_stride) -> dst_out[pair_pos[p]] + pair_k[p]*2LN.
 cudaError_t launch_output(const DevParams &dp, const WavePlan &wp, const u64 *S, size_t S_stride, u32 n_max,
-                          cudaStream_t st);
+                          cudaStream_t st, Profiler *pr = nullptr);
 // Plain coefficient <-> NTT for wally_rotate.
 cudaError_t launch_from_ntt(const DevParams &dp, const u64 *src, u64 *dst, u32 polys_per_item, u32 mod_cycle,
                             u32 n_items, cudaStream_t st);
@@ -76,7 +84,8 @@ cudaError_t launch_gather_wave(const WavePlan &wp, const u32 *sorted_q, const u3
                                u32 num_clusters, u32 wave_begin, u32 wave_len, const u64 *cts, const u64 *keys,
                                const u32 *input_index, const u64 *out_offsets, u64 *out, size_t ct_words,
                                size_t keys_words, cudaStream_t st);
-cudaError_t launch_wave_plan(const WavePlan &wp, const u32 *cluster_chunks, u32 wave_len_max, cudaStream_t st);
+cudaError_t launch_wave_plan(const WavePlan &wp, const u32 *cluster_chunks, u32 wave_len_max, cudaStream_t st,
+                             Profiler *pr = nullptr);
 
 // Setup: encode clusters (Alg. "Server Initialization").
 struct EncodeArgs {

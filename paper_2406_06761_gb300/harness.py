@@ -72,6 +72,15 @@ class DeviceWorkload:
         cr = W.client_randomness(n, self.N, self.q, self.P, self.seed, index=k)
         return W.ClientRandomness(cr.secret[r], cr.key_a[r], cr.key_e[r], cr.enc_a[r], cr.enc_e[r])
 
+    def secrets(self) -> np.ndarray:
+        """Secret keys of every client of the pool, int8 [P][N]."""
+        c = self.pool.chunk
+        parts = []
+        for k in range(0, self.pool_size, c):
+            n = min(c, self.pool_size - k)
+            parts.append(W.ternary(n, self.N, self.seed, f"clients{k // c}/s"))
+        return np.concatenate(parts)
+
     def entry_query(self, e: int) -> np.ndarray | None:
         """Query vector of entry e (None for a fake)."""
         if self.pool.is_fake[e]:

@@ -46,6 +46,10 @@ class wally_info(ctypes.Structure):
     ]
 
 
+class wally_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
 _vp = ctypes.c_void_p
 _u32 = ctypes.c_uint32
 _u64 = ctypes.c_uint64
@@ -65,6 +69,10 @@ SIGNATURES = {
     "wally_keygen": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "wally_encrypt_query": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "wally_decrypt_scores": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
+    "wally_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "wally_profile_read": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_u32)]),
+    "wally_measure_int_peaks": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "wally_last_error": (ctypes.c_char_p, []),
 }
 
@@ -209,6 +217,24 @@ def wally_decrypt_scores(ctx: int, n: int, secret, secret_index, cts, scores, st
     _require_cuda(secret, secret_index, cts, scores)
     _check(load().wally_decrypt_scores(ctx, n, _ptr(secret), _ptr(secret_index), _ptr(cts), _ptr(scores),
                                        _stream(stream)))
+
+
+def wally_profile_enable(ctx: int, enable: bool = True) -> None:
+    _check(load().wally_profile_enable(ctx, 1 if enable else 0))
+
+
+def wally_profile_read(ctx: int) -> dict:
+    """{kernel kind: (launches, total milliseconds)} since profiling was enabled."""
+    arr = (wally_kernel_time * 16)()
+    cnt = _u32()
+    _check(load().wally_profile_read(ctx, ctypes.cast(arr, _vp), 16, ctypes.byref(cnt)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(cnt.value)}
+
+
+def wally_measure_int_peaks(device: int = 0) -> dict:
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().wally_measure_int_peaks(device, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"modmul_per_s": a.value, "butterfly_per_s": b.value, "mac128_per_s": c.value}
 
 
 def wally_last_error() -> str:

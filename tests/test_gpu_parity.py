@@ -130,7 +130,8 @@ def test_encode_parity_chunks_and_degenerate(tiny):
     E = W.embeddings(int(sizes.sum()), prm.d, 15, seed=15)
     Wl.wally_load_clusters(ctx.ptr, sizes, E)
     row = 0
-    for c, s in enumerate(sizes):
+    for c, s in enumerate(sizes.astype(np.int64)):
+        s = int(s)
         m = Wl.wally_cluster_chunks(ctx.ptr, c)
         mo, ref = O.encode_cluster(prm, E[row:row + s])
         assert m == mo
@@ -143,7 +144,7 @@ def test_encode_parity_chunks_and_degenerate(tiny):
 
 def _clusters_ntt(prm, E, sizes):
     res, row = [], 0
-    for s in sizes:
+    for s in (int(x) for x in sizes):
         m, pt = O.encode_cluster(prm, E[row:row + s])
         res.append((m, O.ptxt_to_ntt(prm, m, pt)))
         row += s
@@ -213,14 +214,17 @@ def test_eval_mixed_clusters_ragged_waves(tiny, max_wave):
     got = _np(out)
     ref, ref_off = O.eval_batch(prm, _clusters_ntt(prm, E, sizes), ids, cts[input_index], keys[input_index])
     for q in range(len(ids)):
-        assert np.array_equal(got[offs[q]:offs[q] + m[q]], ref[ref_off[q]:ref_off[q] + m[q]]), q
+        a, b, k = int(offs[q]), int(ref_off[q]), int(m[q])
+        assert np.array_equal(got[a:a + k], ref[b:b + k]), q
     # and the scores decrypt to E q (query 3 uses the fake submission: zeros)
-    row0 = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    sz = sizes.astype(np.int64)
+    row0 = np.concatenate([[0], np.cumsum(sz)[:-1]]).astype(np.int64)
     for q in range(len(ids)):
-        e = input_index[q]
-        Ec = E[row0[ids[q]]:row0[ids[q]] + sizes[ids[q]]].astype(np.int64)
+        e = int(input_index[q])
+        c = int(ids[q])
+        Ec = E[int(row0[c]):int(row0[c] + sz[c])].astype(np.int64)
         expect = Ec @ qs[e].astype(np.int64) if e < 3 else np.zeros(len(Ec), np.int64)
-        sc = np.concatenate([O.decrypt_slots(prm, cr.secret[e], got[offs[q] + k]) for k in range(m[q])])
+        sc = np.concatenate([O.decrypt_slots(prm, cr.secret[e], got[int(offs[q]) + k]) for k in range(int(m[q]))])
         assert np.array_equal(sc[:len(Ec)], expect), q
     ctx.close()
 

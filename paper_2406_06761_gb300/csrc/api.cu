@@ -138,7 +138,7 @@ struct wally_ctx {
 
     // wave workspace
     uint32_t ws_wave = 0, ws_mmax = 0;
-    DevBuf<u64> keysN, ctp, T, S, sc, dg, u;
+    DevBuf<u64> keysN, ctp, T, S, sc, dg, u, dd;
     DevBuf<u32> plan_u32;
     DevBuf<void *> plan_ptr;
     WavePlan wp{};
@@ -178,14 +178,19 @@ int setup_tables(wally_ctx *c)
         const uint64_t psi = (j == c->L + 1) ? c->zeta_t : root_2n(p, c->N);
         if (!psi) return fail(WALLY_EINVAL, "no 2N-th root of unity mod %llu", (unsigned long long)p);
         NttTables t = make_tables(p, psi, c->log_n);
-        std::vector<uint64_t> *arrs[4] = {&t.fwd, &t.fwd_s, &t.inv, &t.inv_s};
-        const u64 *dptr[4];
-        for (int a = 0; a < 4; a++) {
+        // interleaved (w, w') pairs, one 16-byte load per twiddle
+        const Tw *dptr[2];
+        for (int a = 0; a < 2; a++) {
+            std::vector<uint64_t> pairs(2 * (size_t)c->N);
+            for (uint32_t k = 0; k < c->N; k++) {
+                pairs[2 * k] = a ? t.inv[k] : t.fwd[k];
+                pairs[2 * k + 1] = a ? t.inv_s[k] : t.fwd_s[k];
+            }
             void *ptr = nullptr;
-            CUDA_TRY(cudaMalloc(&ptr, 8 * (size_t)c->N));
+            CUDA_TRY(cudaMalloc(&ptr, 16 * (size_t)c->N));
             c->tables.push_back(ptr);
-            CUDA_TRY(cudaMemcpy(ptr, arrs[a]->data(), 8 * (size_t)c->N, cudaMemcpyHostToDevice));
-            dptr[a] = (const u64 *)ptr;
+            CUDA_TRY(cudaMemcpy(ptr, pairs.data(), 16 * (size_t)c->N, cudaMemcpyHostToDevice));
+            dptr[a] = (const Tw *)ptr;
         }
         Mod &md = dp.m[j];
         md.p = p;
@@ -196,9 +201,7 @@ int setup_tables(wally_ctx *c)
         md.n_inv = invmod_h(c->N % p, p);
         md.n_inv_s = shoup_of(md.n_inv, p);
         md.fwd = dptr[0];
-        md.fwd_s = dptr[1];
-        md.inv = dptr[2];
-        md.inv_s = dptr[3];
+        md.inv = dptr[1];
     }
     // CRT constants.  Delta = floor(Q/t) by long division of the product.
     const uint64_t P = c->mods[c->L], t = c->mods[c->L + 1];
@@ -267,11 +270,12 @@ int ensure_workspace(wally_ctx *c, uint32_t W, uint32_t m_max)
     c->sc.release();
     c->dg.release();
     c->u.release();
+    c->dd.release();
     const size_t items = std::max(pairs, (size_t)W);
     if (c->keysN.ensure(W * keysw) != cudaSuccess || c->ctp.ensure(W * (size_t)c->g * ctw) != cudaSuccess ||
         c->T.ensure(pairs * c->h * ctw) != cudaSuccess || c->S.ensure(items * ctw) != cudaSuccess ||
         c->sc.ensure(items * ctw) != cudaSuccess || c->dg.ensure(items * L * N) != cudaSuccess ||
-        c->u.ensure(items * 2 * (L + 1) * N) != cudaSuccess)
+        c->u.ensure(items * 2 * (L + 1) * N) != cudaSuccess || c->dd.ensure(items * (L + 1) * L * N) != cudaSuccess)
         return fail(WALLY_ENOMEM, "cannot allocate the wave workspace (%u queries, %u chunks max)", W, m_max);
     // plan arrays: counts[4] | cluster[W] | pair_pos[P] | pair_k[P] | pair_off[W+1] | seg x3 [W]
     const size_t n32 = 4 + W + 2 * pairs + (W + 1) + 3 * (size_t)W;
@@ -320,6 +324,7 @@ RotArgs rot_args(wally_ctx *c)
     a.sc = c->sc.p;
     a.dg = c->dg.p;
     a.u = c->u.p;
+    a.dd = c->dd.p;
     return a;
 }
 
@@ -348,6 +353,8 @@ int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t s
         a.n_max = wave_len;
         a.n_dev = wp.counts;
         a.galois = c->k1;
+        a.prepared = j > 1;
+        a.next_galois = j + 1 < g ? c->k1 : 0;
         CUDA_TRY(launch_rotate(dp, a, st, c->pr()));
     }
     // a3: T_i = sum_b P'_{k,i,b} ct'[b]
@@ -373,6 +380,8 @@ int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t s
         a.n_max = np_max;
         a.n_dev = wp.counts + 1;
         a.galois = c->kg;
+        a.prepared = i < (int)h - 2;
+        a.next_galois = i > 0 ? c->kg : 0;
         CUDA_TRY(launch_rotate(dp, a, st, c->pr()));
     }
     // a5: back to coefficient form, into the caller's output
@@ -480,6 +489,7 @@ void wally_destroy(wally_ctx *c)
     c->sc.release();
     c->dg.release();
     c->u.release();
+    c->dd.release();
     c->plan_u32.release();
     c->plan_ptr.release();
     c->counts.release();

@@ -26,17 +26,22 @@ typedef unsigned int u32;
 #endif
 #define WALLY_MAX_MODS (WALLY_MAX_LIMBS + 2)
 
-// One RNS modulus with its NTT tables (device pointers, N entries each).
+// A twiddle factor w with its Shoup companion w' = floor(w * 2^64 / p).
+struct __align__(16) Tw {
+    u64 w, ws;
+};
+
+// One RNS modulus with its NTT tables (device pointers, N entries each):
 // fwd[k] = psi^brv(k), inv[k] = psi^-brv(k), brv = bit reversal on log2 N bits.
 struct Mod {
     u64 p, two_p;
     u64 mont_neg_inv;  // -p^-1 mod 2^64
     u64 r2;            // 2^128 mod p
     u64 n_inv, n_inv_s;
-    const u64 *fwd, *fwd_s, *inv, *inv_s;
+    const Tw *fwd, *inv;
 };
 
-// Everything a kernel needs about the parameter set, passed by value.
+// Everything a kernel needs about the parameter set (kept in device memory).
 // Modulus index j: 0..L-1 ciphertext primes q_j, L = P, L+1 = t.
 struct DevParams {
     int log_n, n, L;
@@ -92,11 +97,17 @@ __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 p) { return csub(a + b, 
 __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + p - b; }
 
 // --------------------------------------------------------------------------- NTT
-// One CTA of N/32 threads transforms one polynomial in shared memory.  Each
-// pass loads groups of 2^R elements into registers, runs R butterfly stages,
-// and stores them back; three passes cover log2 N stages.  Shared memory is
-// padded by one word every 16 so that the stride-16 accesses of the last pass
-// do not collide in one bank.
+// One CTA of N/32 threads transforms one polynomial held in shared memory.
+// Each pass loads groups of 2^R elements into registers, runs R butterfly
+// stages, and stores them back; three passes cover log2 N stages.  Shared
+// memory is padded by one word every 16 so that the stride-16 accesses of the
+// last pass do not collide in one bank.
+//
+// Twiddles: stage s uses table entries [2^s, 2^(s+1)).  The entries of the
+// first two passes ([1, 2^(R0+R1)), at most 16 KB) are copied once per CTA
+// into shared memory; the last pass prefetches the 2^R - 1 entries of each
+// group from global memory before touching the group's data, so that their
+// latency overlaps the shared-memory loads instead of stalling each stage.
 
 __host__ __device__ constexpr int smem_words(int n) { return n + n / 16; }
 __device__ __forceinline__ int pidx(int x) { return x + (x >> 4); }
@@ -109,9 +120,19 @@ struct NttShape {
     static constexpr int R0 = (LOGN == 12) ? 4 : 5;
     static constexpr int R1 = (LOGN == 14) ? 5 : 4;
     static constexpr int R2 = LOGN - R0 - R1;
+    // twiddle entries cached in shared memory: the first two passes
+    static constexpr int TW_CACHE = 1 << (R0 + R1);
     // at most 128 registers a thread, so that two CTAs share an SM
     static constexpr int MIN_BLOCKS = 65536 / (T * 128);
 };
+
+// Shared-memory words a kernel needs for one polynomial buffer plus the
+// twiddle caches of `dirs` directions (1 or 2).
+template <int LOGN>
+__host__ __device__ constexpr int ntt_smem_words(int dirs)
+{
+    return smem_words(1 << LOGN) + dirs * 2 * NttShape<LOGN>::TW_CACHE;
+}
 
 __device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 p, u64 two_p)
 {
@@ -128,105 +149,124 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 p, u6
     Y = shoup_mul(x - y + two_p, w, ws, p);
 }
 
+// Copy table entries [0, TW_CACHE) of one direction into shared memory.
+template <int LOGN>
+__device__ __forceinline__ void load_tw_cache(Tw *dst, const Tw *__restrict__ src)
+{
+    constexpr int C = NttShape<LOGN>::TW_CACHE, T = NttShape<LOGN>::T;
+    for (int i = threadIdx.x; i < C; i += T) dst[i] = src[i];
+}
+
 // One butterfly stage ST (0-based inside the pass) on the 2^R registers v of
 // a group.  Stage s = S0 + ST pairs elements 2^(LOGN-1-s) apart (2^(R-1-ST)
 // apart inside the group); the block of element x is x >> (LOGN - s) and its
-// twiddle is table[2^s + block].  All indices are compile-time constants so
-// that v stays in registers.
-template <int S0, int R, int ST, bool FWD>
-__device__ __forceinline__ void ntt_stage(u64 *v, int hi, const u64 *__restrict__ tw, const u64 *__restrict__ tws,
-                                          u64 p, u64 two_p)
+// twiddle is table[2^s + block].  tws: the pass's twiddles, either the shared
+// cache indexed by table position (CACHED) or the group's prefetched list
+// indexed by (2^ST - 1 + block).  All register indices are compile-time
+// constants so that v stays in registers.
+template <int S0, int R, int ST, bool FWD, bool CACHED>
+__device__ __forceinline__ void ntt_stage(u64 *v, int hi, const Tw *tws, u64 p, u64 two_p)
 {
     constexpr int HD = 1 << (R - 1 - ST);
     constexpr int NB = 1 << ST;
 #pragma unroll
     for (int blk = 0; blk < NB; blk++) {
-        const int ti = (1 << (S0 + ST)) + ((hi << ST) | blk);
-        const u64 w = __ldg(tw + ti), ws = __ldg(tws + ti);
+        const Tw t = CACHED ? tws[(1 << (S0 + ST)) + ((hi << ST) | blk)] : tws[(NB - 1) + blk];
 #pragma unroll
         for (int j = 0; j < HD; j++) {
-            if (FWD) ct_bfly(v[blk * 2 * HD + j], v[blk * 2 * HD + j + HD], w, ws, p, two_p);
-            else gs_bfly(v[blk * 2 * HD + j], v[blk * 2 * HD + j + HD], w, ws, p, two_p);
+            if (FWD) ct_bfly(v[blk * 2 * HD + j], v[blk * 2 * HD + j + HD], t.w, t.ws, p, two_p);
+            else gs_bfly(v[blk * 2 * HD + j], v[blk * 2 * HD + j + HD], t.w, t.ws, p, two_p);
         }
     }
 }
 
-template <int S0, int R, int ST>
-__device__ __forceinline__ void ntt_stages_fwd(u64 *v, int hi, const u64 *tw, const u64 *tws, u64 p, u64 two_p)
+template <int S0, int R, int ST, bool CACHED>
+__device__ __forceinline__ void ntt_stages_fwd(u64 *v, int hi, const Tw *tws, u64 p, u64 two_p)
 {
     if constexpr (ST < R) {
-        ntt_stage<S0, R, ST, true>(v, hi, tw, tws, p, two_p);
-        ntt_stages_fwd<S0, R, ST + 1>(v, hi, tw, tws, p, two_p);
+        ntt_stage<S0, R, ST, true, CACHED>(v, hi, tws, p, two_p);
+        ntt_stages_fwd<S0, R, ST + 1, CACHED>(v, hi, tws, p, two_p);
     }
 }
 
-template <int S0, int R, int ST>
-__device__ __forceinline__ void ntt_stages_inv(u64 *v, int hi, const u64 *tw, const u64 *tws, u64 p, u64 two_p)
+template <int S0, int R, int ST, bool CACHED>
+__device__ __forceinline__ void ntt_stages_inv(u64 *v, int hi, const Tw *tws, u64 p, u64 two_p)
 {
     if constexpr (ST >= 0) {
-        ntt_stage<S0, R, ST, false>(v, hi, tw, tws, p, two_p);
-        ntt_stages_inv<S0, R, ST - 1>(v, hi, tw, tws, p, two_p);
+        ntt_stage<S0, R, ST, false, CACHED>(v, hi, tws, p, two_p);
+        ntt_stages_inv<S0, R, ST - 1, CACHED>(v, hi, tws, p, two_p);
     }
 }
 
 // Stages S0 .. S0+R-1 of the forward transform (FWD) or, in reverse order,
 // of the inverse transform, on groups of 2^R elements held in registers.
-template <int LOGN, int S0, int R, bool FWD>
-__device__ __forceinline__ void ntt_pass(u64 *sm, const Mod &md)
+// CACHED: twiddles from the shared cache `tcache`; otherwise from the global
+// table `tglob`, prefetched per group.
+template <int LOGN, int S0, int R, bool FWD, bool CACHED>
+__device__ __forceinline__ void ntt_pass(u64 *sm, const Tw *tcache, const Tw *__restrict__ tglob, u64 p, u64 two_p)
 {
     constexpr int T = NttShape<LOGN>::T;
     constexpr int G = 1 << R;
     constexpr int NG = 32 / G;
     constexpr int BLO = LOGN - R - S0;
     const int tid = threadIdx.x;
-    const u64 p = md.p, two_p = md.two_p;
-    const u64 *tw = FWD ? md.fwd : md.inv;
-    const u64 *tws = FWD ? md.fwd_s : md.inv_s;
 #pragma unroll
     for (int u = 0; u < NG; u++) {
         const int gi = tid + T * u;
         const int lo = gi & ((1 << BLO) - 1);
         const int hi = gi >> BLO;
         const int base = (hi << (BLO + R)) | lo;
+        Tw tw[CACHED ? 1 : G - 1];
+        if constexpr (!CACHED) {
+#pragma unroll
+            for (int st = 0, k = 0; st < R; st++)
+#pragma unroll
+                for (int blk = 0; blk < (1 << st); blk++, k++) tw[k] = tglob[(1 << (S0 + st)) + ((hi << st) | blk)];
+        }
+        // element x = base + (k << BLO) lives at pidx(x) = pidx(base) + k*2^BLO + (k*2^BLO >> 4)
+        const int sb = pidx(base);
         u64 v[G];
 #pragma unroll
-        for (int k = 0; k < G; k++) v[k] = sm[pidx(base + (k << BLO))];
-        if constexpr (FWD) ntt_stages_fwd<S0, R, 0>(v, hi, tw, tws, p, two_p);
-        else ntt_stages_inv<S0, R, R - 1>(v, hi, tw, tws, p, two_p);
+        for (int k = 0; k < G; k++) v[k] = sm[sb + (k << BLO) + ((k << BLO) >> 4)];
+        if constexpr (FWD) ntt_stages_fwd<S0, R, 0, CACHED>(v, hi, CACHED ? tcache : tw, p, two_p);
+        else ntt_stages_inv<S0, R, R - 1, CACHED>(v, hi, CACHED ? tcache : tw, p, two_p);
 #pragma unroll
-        for (int k = 0; k < G; k++) sm[pidx(base + (k << BLO))] = v[k];
+        for (int k = 0; k < G; k++) sm[sb + (k << BLO) + ((k << BLO) >> 4)] = v[k];
     }
 }
 
 // Forward negacyclic NTT in place: natural-order coefficients (any values
 // < 4p) -> evaluations at psi^(2*brv(i)+1) in bit-reversed position i, values
-// in [0, 4p).  Ends with __syncthreads().
+// in [0, 4p).  tcache: this direction's shared twiddle cache (load_tw_cache,
+// made visible by a barrier before the call).  Ends with __syncthreads().
 template <int LOGN>
-__device__ __forceinline__ void ntt_fwd(u64 *sm, const Mod &md)
+__device__ __forceinline__ void ntt_fwd(u64 *sm, const Tw *tcache, const Mod &md)
 {
     using S = NttShape<LOGN>;
+    const u64 p = md.p, two_p = md.two_p;
     __syncthreads();
-    ntt_pass<LOGN, 0, S::R0, true>(sm, md);
+    ntt_pass<LOGN, 0, S::R0, true, true>(sm, tcache, md.fwd, p, two_p);
     __syncthreads();
-    ntt_pass<LOGN, S::R0, S::R1, true>(sm, md);
+    ntt_pass<LOGN, S::R0, S::R1, true, true>(sm, tcache, md.fwd, p, two_p);
     __syncthreads();
-    ntt_pass<LOGN, S::R0 + S::R1, S::R2, true>(sm, md);
+    ntt_pass<LOGN, S::R0 + S::R1, S::R2, true, false>(sm, tcache, md.fwd, p, two_p);
     __syncthreads();
 }
 
 // Inverse: bit-reversed evaluations (values < 2p) -> natural-order
 // coefficients times N (values in [0, 2p)); callers scale by N^-1 with
-// finish_inv().  Ends with __syncthreads().
+// inv_finish().  Ends with __syncthreads().
 template <int LOGN>
-__device__ __forceinline__ void ntt_inv(u64 *sm, const Mod &md)
+__device__ __forceinline__ void ntt_inv(u64 *sm, const Tw *tcache, const Mod &md)
 {
     using S = NttShape<LOGN>;
+    const u64 p = md.p, two_p = md.two_p;
     __syncthreads();
-    ntt_pass<LOGN, S::R0 + S::R1, S::R2, false>(sm, md);
+    ntt_pass<LOGN, S::R0 + S::R1, S::R2, false, false>(sm, tcache, md.inv, p, two_p);
     __syncthreads();
-    ntt_pass<LOGN, S::R0, S::R1, false>(sm, md);
+    ntt_pass<LOGN, S::R0, S::R1, false, true>(sm, tcache, md.inv, p, two_p);
     __syncthreads();
-    ntt_pass<LOGN, 0, S::R0, false>(sm, md);
+    ntt_pass<LOGN, 0, S::R0, false, true>(sm, tcache, md.inv, p, two_p);
     __syncthreads();
 }
 
@@ -245,4 +285,34 @@ __device__ __forceinline__ u32 galois_src(u32 j, u64 k, int log_n)
     const u32 mask2n = (2u << log_n) - 1;
     u32 e = (u32)(((u64)(2 * brv(j, log_n) + 1) * k) & mask2n);
     return brv((e - 1) >> 1, log_n);
+}
+
+// --------------------------------------------------------------------------- element IO
+// Elementwise sweeps use pairs: thread t owns elements 2(t + T*u) and
+// 2(t + T*u) + 1 for u < 16, so that global accesses are 16-byte and
+// coalesced.  Both elements of a pair sit in the same 16-word smem row.
+template <int LOGN>
+__device__ __forceinline__ int pair_elem(int u)
+{
+    return 2 * ((int)threadIdx.x + NttShape<LOGN>::T * u);
+}
+
+__device__ __forceinline__ ulonglong2 ldg2(const u64 *p) { return __ldg(reinterpret_cast<const ulonglong2 *>(p)); }
+__device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
+__device__ __forceinline__ void st2(u64 *p, u64 a, u64 b) { *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(a, b); }
+
+// Global polynomial -> shared buffer (any values), 16-byte loads.  COHERENT:
+// the data was written earlier by this kernel (read through the coherent
+// path, not the read-only cache).
+template <int LOGN, bool COHERENT = false>
+__device__ __forceinline__ void poly_load(u64 *sm, const u64 *g)
+{
+#pragma unroll 4
+    for (int u = 0; u < 16; u++) {
+        const int e = pair_elem<LOGN>(u);
+        const ulonglong2 v = COHERENT ? ld2(g + e) : ldg2(g + e);
+        const int s = pidx(e);
+        sm[s] = v.x;
+        sm[s + 1] = v.y;
+    }
 }

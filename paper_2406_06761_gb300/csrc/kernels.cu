@@ -1,16 +1,15 @@
-// kernels.cu -- device kernels of the Wally GB300 library.
+// kernels.cu -- device kernels of the Wally GB300 library (evaluation path).
 //
 // Paper steps (arXiv 2406.06761) and where they run:
 //   a0 grouping of the batch by cluster ......... k_hist / k_scan_clusters / k_scatter, k_gather_wave, k_wave_plan
 //   a1 inputs to NTT form ....................... k_to_ntt
 //   a2/a4 rotations Rot_k (Sec. 2 CtRotate, hybrid key switching Sec. 7)
-//        ......................................... k_ks_a (automorphism + INTT of c1 -> digits)
+//        ......................................... k_ks_a (automorphism + INTT of c1 -> digits; first of a chain)
 //                                                  k_ks_b (digit NTTs + inner product with the key)
-//                                                  k_ks_c (ModDown, + sigma(c0), + T_i for Horner)
+//                                                  k_ks_c (ModDown, + sigma(c0), + T_i for Horner; then the
+//                                                          next rotation's automorphism and digits)
 //   a3 plaintext x ciphertext products (Alg. "Server Computation") ... k_mac
 //   a5 output to coefficient form ............... k_output
-//   setup: cluster encoding (Alg. "Server Initialization") ... k_encode_cluster
-//   client side: k_encode_query, k_encrypt, k_keygen, k_decrypt_*
 #include <cstdio>
 #include "kernels.hpp"
 
@@ -18,7 +17,6 @@ namespace wally {
 
 namespace {
 
-template <int LOGN>
 __device__ __forceinline__ void load_mod(Mod *s, const DevParams *dpp, int j)
 {
     if (threadIdx.x < sizeof(Mod) / 8) ((u64 *)s)[threadIdx.x] = ((const u64 *)&dpp->m[j])[threadIdx.x];
@@ -32,8 +30,21 @@ __device__ __forceinline__ u32 item_count(u32 n_max, const u32 *n_dev)
     return c < n_max ? c : n_max;
 }
 
+// Shared memory of the transform kernels: one padded polynomial buffer and the
+// twiddle caches of both directions.
+template <int LOGN>
+struct Smem {
+    u64 *poly;
+    Tw *twf, *twi;
+    __device__ __forceinline__ explicit Smem(u64 *base)
+    {
+        poly = base;
+        twf = reinterpret_cast<Tw *>(base + smem_words(1 << LOGN));
+        twi = twf + NttShape<LOGN>::TW_CACHE;
+    }
+};
+
 #define NTT_LB(LOGN) __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::MIN_BLOCKS)
-#define NTT_LB_WIDE(LOGN) __launch_bounds__(NttShape<LOGN>::T)
 
 // ---------------------------------------------------------------- a1: to NTT form
 // Item x, polynomial z (modulus z % mod_cycle): forward NTT of the input
@@ -43,26 +54,28 @@ __global__ void NTT_LB(LOGN) k_to_ntt(const DevParams *dpp, const u64 *const *sr
                                       size_t src_stride, u64 *dst, size_t dst_stride, u32 mod_cycle, u32 n_max,
                                       const u32 *n_dev, bool mont)
 {
-    constexpr int N = 1 << LOGN, T = N / 32;
-    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN;
+    extern __shared__ u64 smraw[];
+    Smem<LOGN> S(smraw);
     __shared__ Mod md;
     const u32 x = blockIdx.x;
     if (x >= item_count(n_max, n_dev)) return;
     const u32 z = blockIdx.y;
-    load_mod<LOGN>(&md, dpp, z % mod_cycle);
+    load_mod(&md, dpp, z % mod_cycle);
+    load_tw_cache<LOGN>(S.twf, md.fwd);
     const u64 *s = (src_ptrs ? src_ptrs[x] : src + x * src_stride) + (size_t)z * N;
     u64 *d = dst + x * dst_stride + (size_t)z * N;
-#pragma unroll 8
-    for (int u = 0; u < 32; u++) {
-        int e = threadIdx.x + T * u;
-        sm[pidx(e)] = s[e];
-    }
-    ntt_fwd<LOGN>(sm, md);
-#pragma unroll 8
-    for (int u = 0; u < 32; u++) {
-        int e = threadIdx.x + T * u;
-        u64 v = fwd_finish(sm[pidx(e)], md);
-        d[e] = mont ? mont_mul(v, md.r2, md) : v;
+    poly_load<LOGN>(S.poly, s);
+    ntt_fwd<LOGN>(S.poly, S.twf, md);
+#pragma unroll 4
+    for (int u = 0; u < 16; u++) {
+        const int e = pair_elem<LOGN>(u), sp = pidx(e);
+        u64 a = fwd_finish(S.poly[sp], md), b = fwd_finish(S.poly[sp + 1], md);
+        if (mont) {
+            a = mont_mul(a, md.r2, md);
+            b = mont_mul(b, md.r2, md);
+        }
+        st2(d + e, a, b);
     }
 }
 
@@ -70,179 +83,207 @@ __global__ void NTT_LB(LOGN) k_to_ntt(const DevParams *dpp, const u64 *const *sr
 template <int LOGN>
 __global__ void NTT_LB(LOGN) k_from_ntt(const DevParams *dpp, const u64 *src, u64 *dst, u32 polys, u32 mod_cycle)
 {
-    constexpr int N = 1 << LOGN, T = N / 32;
-    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN;
+    extern __shared__ u64 smraw[];
+    Smem<LOGN> S(smraw);
     __shared__ Mod md;
     const u32 x = blockIdx.x, z = blockIdx.y;
-    load_mod<LOGN>(&md, dpp, z % mod_cycle);
+    load_mod(&md, dpp, z % mod_cycle);
+    load_tw_cache<LOGN>(S.twi, md.inv);
     const u64 *s = src + ((size_t)x * polys + z) * N;
     u64 *d = dst + ((size_t)x * polys + z) * N;
-#pragma unroll 8
-    for (int u = 0; u < 32; u++) {
-        int e = threadIdx.x + T * u;
-        sm[pidx(e)] = s[e];
-    }
-    ntt_inv<LOGN>(sm, md);
-#pragma unroll 8
-    for (int u = 0; u < 32; u++) {
-        int e = threadIdx.x + T * u;
-        d[e] = inv_finish(sm[pidx(e)], md);
+    poly_load<LOGN>(S.poly, s);
+    ntt_inv<LOGN>(S.poly, S.twi, md);
+#pragma unroll 4
+    for (int u = 0; u < 16; u++) {
+        const int e = pair_elem<LOGN>(u), sp = pidx(e);
+        st2(d + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp + 1], md));
     }
 }
 
 // ---------------------------------------------------------------- a2/a4: rotations
-// k_ks_a, CTA (item x, limb i): sigma_k on limb i of both components (a
-// permutation in the NTT domain), written to sc; INTT of sigma(c1)_i gives the
-// digit d_i = [sigma(c1)]_{q_i} in [0, q_i) (reading R3: non-centred).
+// Shared tail of k_ks_a and the fused part of k_ks_c.  The buffer holds limb
+// j of component c of a ciphertext (NTT form); write sigma_k of it to sc and,
+// for c = 1, the digit d_j = [sigma(c1)]_{q_j} in [0, q_j) (reading R3:
+// non-centred) to dg.  sigma_k is a permutation of the NTT positions.
 template <int LOGN>
-__global__ void NTT_LB(LOGN) k_ks_a(const DevParams *dpp, RotArgs a)
+__device__ __forceinline__ void permute_and_digit(const Smem<LOGN> &S, const Mod &md, u64 k, int c, u64 *sc_cj,
+                                                  u64 *dg_j)
 {
-    constexpr int N = 1 << LOGN, T = N / 32;
-    extern __shared__ u64 sm[];
-    __shared__ Mod md;
-    const u32 x = blockIdx.x;
-    if (x >= item_count(a.n_max, a.n_dev)) return;
-    const int i = blockIdx.y, L = dpp->L;
-    load_mod<LOGN>(&md, dpp, i);
-    const u64 *src = a.src + x * a.src_stride;
-    u64 *sc = a.sc + (size_t)x * 2 * L * N;
-    for (int c = 0; c < 2; c++) {
-        const u64 *s = src + ((size_t)c * L + i) * N;
+    __syncthreads();
+#pragma unroll 4
+    for (int u = 0; u < 16; u++) {
+        const int e = pair_elem<LOGN>(u);
+        st2(sc_cj + e, S.poly[pidx(galois_src(e, k, LOGN))], S.poly[pidx(galois_src(e + 1, k, LOGN))]);
+    }
+    if (c == 1) {
         __syncthreads();
-#pragma unroll 8
-        for (int u = 0; u < 32; u++) {
-            int e = threadIdx.x + T * u;
-            sm[pidx(e)] = s[e];
-        }
-        __syncthreads();
-        u64 v[32];
-#pragma unroll
-        for (int u = 0; u < 32; u++) {
-            int e = threadIdx.x + T * u;
-            v[u] = sm[pidx(galois_src(e, a.galois, LOGN))];
-        }
-        u64 *dsc = sc + ((size_t)c * L + i) * N;
-#pragma unroll
-        for (int u = 0; u < 32; u++) dsc[threadIdx.x + T * u] = v[u];
-        if (c == 1) {
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < 32; u++) sm[pidx(threadIdx.x + T * u)] = v[u];
-            ntt_inv<LOGN>(sm, md);
-            u64 *dd = a.dg + ((size_t)x * L + i) * N;
-#pragma unroll 8
-            for (int u = 0; u < 32; u++) {
-                int e = threadIdx.x + T * u;
-                dd[e] = inv_finish(sm[pidx(e)], md);
-            }
+        poly_load<LOGN, true>(S.poly, sc_cj);  // this CTA's own writes
+        ntt_inv<LOGN>(S.poly, S.twi, md);
+#pragma unroll 4
+        for (int u = 0; u < 16; u++) {
+            const int e = pair_elem<LOGN>(u), sp = pidx(e);
+            st2(dg_j + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp + 1], md));
         }
     }
 }
 
-// k_ks_b, CTA (item x, modulus j in q_0..q_{L-1}, P): u_j = sum_i NTT_j(d_i) * key_{i,j}
-// for both key components.  For j = P the sums are brought back to
-// coefficients (r = [u]_P) for ModDown.
+// k_ks_a, CTA (item x, limb j, component c): first rotation of a chain.
+template <int LOGN>
+__global__ void NTT_LB(LOGN) k_ks_a(const DevParams *dpp, RotArgs a)
+{
+    constexpr int N = 1 << LOGN;
+    extern __shared__ u64 smraw[];
+    Smem<LOGN> S(smraw);
+    __shared__ Mod md;
+    const u32 x = blockIdx.x;
+    if (x >= item_count(a.n_max, a.n_dev)) return;
+    const int L = dpp->L, j = blockIdx.y % L, c = blockIdx.y / L;
+    load_mod(&md, dpp, j);
+    if (c == 1) load_tw_cache<LOGN>(S.twi, md.inv);
+    poly_load<LOGN>(S.poly, a.src + x * a.src_stride + ((size_t)c * L + j) * N);
+    permute_and_digit<LOGN>(S, md, a.galois, c, a.sc + ((size_t)x * 2 * L + c * L + j) * N,
+                            a.dg + ((size_t)x * L + j) * N);
+}
+
+// k_ks_b, CTA (item x, modulus j in q_0..q_{L-1}, P):
+//   u_j = sum_i NTT_j(d_i) * key_{i,j}  for both key components,
+// as one lazy 128-bit sum per output and a single Montgomery reduction (the
+// key is stored times 2^64).  NTT_j(d_j) = sigma(c1)_j is already known; the
+// other digits are transformed here, all but the last one parked in dd.  For
+// j = P the sums are brought back to coefficients (r = [u]_P) for ModDown.
 template <int LOGN>
 __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
 {
-    constexpr int N = 1 << LOGN, T = N / 32;
-    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN;
+    extern __shared__ u64 smraw[];
+    Smem<LOGN> S(smraw);
     __shared__ Mod md;
     const u32 x = blockIdx.x;
     if (x >= item_count(a.n_max, a.n_dev)) return;
     const int j = blockIdx.y, L = dpp->L;
-    load_mod<LOGN>(&md, dpp, j);
+    load_mod(&md, dpp, j);
+    load_tw_cache<LOGN>(S.twf, md.fwd);
+    if (j == L) load_tw_cache<LOGN>(S.twi, md.inv);
     const u64 *kx = a.key + (size_t)(a.key_map ? a.key_map[x] : x) * a.key_stride;
+    u64 *dd = a.dd + ((size_t)x * (L + 1) + j) * L * N;
+    const int last = (j == L - 1) ? L - 2 : L - 1;  // the last digit transformed here
+    for (int i = 0; i < L; i++) {
+        if (i == j) continue;
+        __syncthreads();
+        poly_load<LOGN>(S.poly, a.dg + ((size_t)x * L + i) * N);  // < q_i < 4 p_j
+        ntt_fwd<LOGN>(S.poly, S.twf, md);
+        if (i != last) {
+            u64 *di = dd + (size_t)i * N;
+#pragma unroll 4
+            for (int u = 0; u < 16; u++) {
+                const int e = pair_elem<LOGN>(u), sp = pidx(e);
+                st2(di + e, S.poly[sp], S.poly[sp + 1]);  // lazy, < 4 p_j
+            }
+        }
+    }
     u64 *u0 = a.u + ((size_t)x * 2 + 0) * (L + 1) * N + (size_t)j * N;
     u64 *u1 = a.u + ((size_t)x * 2 + 1) * (L + 1) * N + (size_t)j * N;
-    const u64 p = md.p;
-    for (int i = 0; i < L; i++) {
-        const u64 *kb = kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N;
-        const u64 *ka = kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N;
-        const u64 *D = nullptr;
-        if (i == j) {
-            D = a.sc + ((size_t)x * 2 * L + L + i) * N;  // sigma(c1)_i, already NTT form mod q_i
-        } else {
-            const u64 *dg = a.dg + ((size_t)x * L + i) * N;
-            __syncthreads();
-#pragma unroll 8
-            for (int u = 0; u < 32; u++) {
-                int e = threadIdx.x + T * u;
-                sm[pidx(e)] = dg[e];  // < q_i < 4p_j
+    const u64 *sc1 = a.sc + ((size_t)x * 2 * L + L + j) * N;
+#pragma unroll 2
+    for (int u = 0; u < 16; u++) {
+        const int e = pair_elem<LOGN>(u), sp = pidx(e);
+        u64 h0a = 0, l0a = 0, h0b = 0, l0b = 0, h1a = 0, l1a = 0, h1b = 0, l1b = 0;
+        for (int i = 0; i < L; i++) {
+            u64 da, db;
+            if (i == j) {
+                const ulonglong2 t = ld2(sc1 + e);
+                da = t.x;
+                db = t.y;
+            } else if (i == last) {
+                da = S.poly[sp];
+                db = S.poly[sp + 1];
+            } else {
+                const ulonglong2 t = ld2(dd + (size_t)i * N + e);
+                da = t.x;
+                db = t.y;
             }
-            ntt_fwd<LOGN>(sm, md);
+            const ulonglong2 kb = ldg2(kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N + e);
+            const ulonglong2 ka = ldg2(kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N + e);
+            mac128(h0a, l0a, da, kb.x);
+            mac128(h0b, l0b, db, kb.y);
+            mac128(h1a, l1a, da, ka.x);
+            mac128(h1b, l1b, db, ka.y);
         }
-#pragma unroll 4
-        for (int u = 0; u < 32; u++) {
-            int e = threadIdx.x + T * u;
-            u64 d = D ? D[e] : sm[pidx(e)];
-            u64 t0 = mont_mul(d, kb[e], md), t1 = mont_mul(d, ka[e], md);
-            if (i > 0) {
-                t0 = addmod(t0, u0[e], p);
-                t1 = addmod(t1, u1[e], p);
-            }
-            u0[e] = t0;
-            u1[e] = t1;
-        }
+        st2(u0 + e, mont_redc(h0a, l0a, md), mont_redc(h0b, l0b, md));
+        st2(u1 + e, mont_redc(h1a, l1a, md), mont_redc(h1b, l1b, md));
     }
     if (j == L) {
         for (int c = 0; c < 2; c++) {
             u64 *uc = c ? u1 : u0;
             __syncthreads();
-#pragma unroll 8
-            for (int u = 0; u < 32; u++) {
-                int e = threadIdx.x + T * u;
-                sm[pidx(e)] = uc[e];
-            }
-            ntt_inv<LOGN>(sm, md);
-#pragma unroll 8
-            for (int u = 0; u < 32; u++) {
-                int e = threadIdx.x + T * u;
-                uc[e] = inv_finish(sm[pidx(e)], md);
+            poly_load<LOGN, true>(S.poly, uc);
+            ntt_inv<LOGN>(S.poly, S.twi, md);
+#pragma unroll 4
+            for (int u = 0; u < 16; u++) {
+                const int e = pair_elem<LOGN>(u), sp = pidx(e);
+                st2(uc + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp + 1], md));
             }
         }
     }
 }
 
-// k_ks_c, CTA (item x, limb j): ModDown (reading R4: round to nearest through
-// the centred residue r_c of u mod P): u'_j = (u_j - NTT_j(r_c)) * P^-1, then
-// out = (sigma(c0)_j + u0'_j [+ T0_j], u1'_j [+ T1_j]).
+// k_ks_c, CTA (item x, limb j, component c): ModDown (reading R4: round to
+// nearest through the centred residue r_c of u mod P):
+//   u'_j = (u_j - NTT_j(r_c)) * P^-1 mod q_j,
+//   out_0 = sigma(c0)_j + u0'_j [+ T0_j],  out_1 = u1'_j [+ T1_j].
+// With next_galois set, the output is also prepared as the input of the next
+// rotation of the chain (its automorphism and, for c = 1, its digit).
 template <int LOGN>
 __global__ void NTT_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
 {
-    constexpr int N = 1 << LOGN, T = N / 32;
-    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN;
+    extern __shared__ u64 smraw[];
+    Smem<LOGN> S(smraw);
     __shared__ Mod md;
     const u32 x = blockIdx.x;
     if (x >= item_count(a.n_max, a.n_dev)) return;
-    const int j = blockIdx.y, L = dpp->L;
-    load_mod<LOGN>(&md, dpp, j);
+    const int L = dpp->L, j = blockIdx.y % L, c = blockIdx.y / L;
+    load_mod(&md, dpp, j);
+    load_tw_cache<LOGN>(S.twf, md.fwd);
+    if (a.next_galois && c == 1) load_tw_cache<LOGN>(S.twi, md.inv);
     const u64 q = md.p, P = dpp->m[L].p, half = (P - 1) / 2;
     const u64 pinv = dpp->pinv[j], pinv_s = dpp->pinv_s[j];
-    for (int c = 0; c < 2; c++) {
-        const u64 *r = a.u + (((size_t)x * 2 + c) * (L + 1) + L) * N;
-        __syncthreads();
-#pragma unroll 8
-        for (int u = 0; u < 32; u++) {
-            int e = threadIdx.x + T * u;
-            u64 rv = r[e];
-            sm[pidx(e)] = rv > half ? q - (P - rv) : rv;  // r_c mod q_j, value < 4q
-        }
-        ntt_fwd<LOGN>(sm, md);
-        const u64 *uj = a.u + (((size_t)x * 2 + c) * (L + 1) + j) * N;
-        const u64 *s0 = a.sc + ((size_t)x * 2 * L + j) * N;
-        const u64 *ad = a.add ? a.add + x * a.add_stride + ((size_t)c * L + j) * N : nullptr;
-        u64 *dst = a.dst + x * a.dst_stride + ((size_t)c * L + j) * N;
+    const u64 *r = a.u + (((size_t)x * 2 + c) * (L + 1) + L) * N;
 #pragma unroll 4
-        for (int u = 0; u < 32; u++) {
-            int e = threadIdx.x + T * u;
-            u64 R = fwd_finish(sm[pidx(e)], md);
-            u64 v = csub(shoup_mul(uj[e] + q - R, pinv, pinv_s, q), q);
-            if (c == 0) v = addmod(v, s0[e], q);
-            if (ad) v = addmod(v, ad[e], q);
-            dst[e] = v;
-        }
+    for (int u = 0; u < 16; u++) {
+        const int e = pair_elem<LOGN>(u), sp = pidx(e);
+        const ulonglong2 rv = ldg2(r + e);
+        S.poly[sp] = rv.x > half ? q - (P - rv.x) : rv.x;  // r_c mod q_j, < 4q
+        S.poly[sp + 1] = rv.y > half ? q - (P - rv.y) : rv.y;
     }
+    ntt_fwd<LOGN>(S.poly, S.twf, md);
+    const u64 *uj = a.u + (((size_t)x * 2 + c) * (L + 1) + j) * N;
+    u64 *sc_cj = a.sc + ((size_t)x * 2 * L + c * L + j) * N;
+    const u64 *ad = a.add ? a.add + x * a.add_stride + ((size_t)c * L + j) * N : nullptr;
+    u64 *dst = a.dst + x * a.dst_stride + ((size_t)c * L + j) * N;
+#pragma unroll 4
+    for (int u = 0; u < 16; u++) {
+        const int e = pair_elem<LOGN>(u), sp = pidx(e);
+        const ulonglong2 uv = ldg2(uj + e);
+        u64 v0 = csub(shoup_mul(uv.x + q - fwd_finish(S.poly[sp], md), pinv, pinv_s, q), q);
+        u64 v1 = csub(shoup_mul(uv.y + q - fwd_finish(S.poly[sp + 1], md), pinv, pinv_s, q), q);
+        if (c == 0) {
+            const ulonglong2 s0 = ld2(sc_cj + e);
+            v0 = addmod(v0, s0.x, q);
+            v1 = addmod(v1, s0.y, q);
+        }
+        if (ad) {
+            const ulonglong2 t = ldg2(ad + e);
+            v0 = addmod(v0, t.x, q);
+            v1 = addmod(v1, t.y, q);
+        }
+        st2(dst + e, v0, v1);
+        S.poly[sp] = v0;  // same thread, same positions: the output replaces NTT(r)
+        S.poly[sp + 1] = v1;
+    }
+    if (a.next_galois)
+        permute_and_digit<LOGN>(S, md, a.next_galois, c, sc_cj, a.dg + ((size_t)x * L + j) * N);
 }
 
 // ---------------------------------------------------------------- a3: PtCt products
@@ -317,28 +358,26 @@ __global__ void __launch_bounds__(256) k_mac(const DevParams *dpp, ClusterStore 
 
 // ---------------------------------------------------------------- a5: output
 template <int LOGN>
-__global__ void NTT_LB(LOGN) k_output(const DevParams *dpp, WavePlan wp, const u64 *S, size_t S_stride, u32 n_max)
+__global__ void NTT_LB(LOGN) k_output(const DevParams *dpp, WavePlan wp, const u64 *S_, size_t S_stride, u32 n_max)
 {
-    constexpr int N = 1 << LOGN, T = N / 32;
-    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN;
+    extern __shared__ u64 smraw[];
+    Smem<LOGN> S(smraw);
     __shared__ Mod md;
     const u32 p = blockIdx.x;
     if (p >= item_count(n_max, wp.counts + 1)) return;
     const int L = dpp->L;
     const int z = blockIdx.y, l = z % L;
-    load_mod<LOGN>(&md, dpp, l);
-    const u64 *s = S + p * S_stride + (size_t)z * N;
+    load_mod(&md, dpp, l);
+    load_tw_cache<LOGN>(S.twi, md.inv);
+    const u64 *s = S_ + p * S_stride + (size_t)z * N;
     u64 *d = wp.dst_out[wp.pair_pos[p]] + (size_t)wp.pair_k[p] * 2 * L * N + (size_t)z * N;
-#pragma unroll 8
-    for (int u = 0; u < 32; u++) {
-        int e = threadIdx.x + T * u;
-        sm[pidx(e)] = s[e];
-    }
-    ntt_inv<LOGN>(sm, md);
-#pragma unroll 8
-    for (int u = 0; u < 32; u++) {
-        int e = threadIdx.x + T * u;
-        d[e] = inv_finish(sm[pidx(e)], md);
+    poly_load<LOGN>(S.poly, s);
+    ntt_inv<LOGN>(S.poly, S.twi, md);
+#pragma unroll 4
+    for (int u = 0; u < 16; u++) {
+        const int e = pair_elem<LOGN>(u), sp = pidx(e);
+        st2(d + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp + 1], md));
     }
 }
 
@@ -462,7 +501,7 @@ cudaError_t set_smem(K kernel, size_t bytes)
 template <int LOGN>
 cudaError_t set_attrs_logn()
 {
-    const size_t sb = smem_words(1 << LOGN) * 8;
+    const size_t sb = ntt_smem_words<LOGN>(2) * 8;
     cudaError_t e = cudaSuccess;
 #define SA(k) if (e == cudaSuccess) e = set_smem(k<LOGN>, sb)
     SA(k_to_ntt);
@@ -485,7 +524,7 @@ cudaError_t set_attrs_logn()
     default: return cudaErrorInvalidValue;          \
     }
 
-static inline size_t smem_bytes(int log_n) { return smem_words(1 << log_n) * 8; }
+#define SMEM(LG) (ntt_smem_words<LG>(2) * 8)
 static inline int ntt_threads(int log_n) { return (1 << log_n) / 32; }
 
 cudaError_t set_client_kernel_attributes(int log_n);
@@ -529,7 +568,7 @@ cudaError_t launch_to_ntt(const DevParams &dp, const u64 *const *src_ptrs, const
     const DevParams *dpp = device_params_of(dp);
     dim3 grid(n_max, polys);
     ProfScope ps(pr, KK_TO_NTT, st);
-    DISPATCH_LOGN(dp.log_n, (k_to_ntt<LG><<<grid, ntt_threads(LG), smem_bytes(LG), st>>>(
+    DISPATCH_LOGN(dp.log_n, (k_to_ntt<LG><<<grid, ntt_threads(LG), SMEM(LG), st>>>(
                                 dpp, src_ptrs, src, src_stride, dst, dst_stride, mod_cycle, n_max, n_dev, mont)));
     return cudaGetLastError();
 }
@@ -540,8 +579,7 @@ cudaError_t launch_from_ntt(const DevParams &dp, const u64 *src, u64 *dst, u32 p
     if (n_items == 0) return cudaSuccess;
     const DevParams *dpp = device_params_of(dp);
     dim3 grid(n_items, polys);
-    DISPATCH_LOGN(dp.log_n, (k_from_ntt<LG><<<grid, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, src, dst, polys,
-                                                                                              mod_cycle)));
+    DISPATCH_LOGN(dp.log_n, (k_from_ntt<LG><<<grid, ntt_threads(LG), SMEM(LG), st>>>(dpp, src, dst, polys, mod_cycle)));
     return cudaGetLastError();
 }
 
@@ -551,17 +589,17 @@ cudaError_t launch_rotate(const DevParams &dp, const RotArgs &a, cudaStream_t st
     const DevParams *dpp = device_params_of(dp);
     const int L = dp.L;
     DISPATCH_LOGN(dp.log_n, ({
-                      {
+                      if (!a.prepared) {
                           ProfScope ps(pr, KK_KS_A, st);
-                          k_ks_a<LG><<<dim3(a.n_max, L), ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a);
+                          k_ks_a<LG><<<dim3(a.n_max, 2 * L), ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
                       }
                       {
                           ProfScope ps(pr, KK_KS_B, st);
-                          k_ks_b<LG><<<dim3(a.n_max, L + 1), ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a);
+                          k_ks_b<LG><<<dim3(a.n_max, L + 1), ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
                       }
                       {
                           ProfScope ps(pr, KK_KS_C, st);
-                          k_ks_c<LG><<<dim3(a.n_max, L), ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a);
+                          k_ks_c<LG><<<dim3(a.n_max, 2 * L), ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
                       }
                   }));
     return cudaGetLastError();
@@ -595,8 +633,8 @@ cudaError_t launch_output(const DevParams &dp, const WavePlan &wp, const u64 *S,
     if (n_max == 0) return cudaSuccess;
     const DevParams *dpp = device_params_of(dp);
     ProfScope ps(pr, KK_OUTPUT, st);
-    DISPATCH_LOGN(dp.log_n, (k_output<LG><<<dim3(n_max, 2 * dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
-                                dpp, wp, S, S_stride, n_max)));
+    DISPATCH_LOGN(dp.log_n, (k_output<LG><<<dim3(n_max, 2 * dp.L), ntt_threads(LG), SMEM(LG), st>>>(dpp, wp, S,
+                                                                                                    S_stride, n_max)));
     return cudaGetLastError();
 }
 

@@ -12,8 +12,12 @@ namespace wally {
 // when add != nullptr (the Horner step S = Rot_g(S) + T_i), and uses the key
 // (NTT form, Montgomery scaled, [L][2][L+1][N]) at
 // key + (key_map ? key_map[x] : x) * key_stride.  Item count: *n_dev when
-// n_dev != nullptr (bounded by n_max), else n_max.  Scratch sc [n][2][L][N],
-// dg [n][L][N], u [n][2][L+1][N].
+// n_dev != nullptr (bounded by n_max), else n_max.  Scratch sc [n][2][L][N]
+// (the automorphism of the input, NTT form), dg [n][L][N] (digits),
+// u [n][2][L+1][N] (key products), dd [n][L+1][L][N] (transformed digits).
+// prepared: sc and dg already hold this rotation's input (the previous
+// rotation of the chain wrote them), so src is not read.  next_galois != 0:
+// also prepare sc and dg for a following rotation by that element.
 struct RotArgs {
     const u64 *src;
     size_t src_stride;
@@ -27,7 +31,9 @@ struct RotArgs {
     u32 n_max;
     const u32 *n_dev;
     u64 galois;
-    u64 *sc, *dg, *u;
+    u64 next_galois;
+    bool prepared;
+    u64 *sc, *dg, *u, *dd;
 };
 
 // Per-wave plan, all device arrays sized for max_wave queries (pairs: x m_max).

@@ -10,7 +10,6 @@ namespace wally {
 namespace {
 
 
-template <int LOGN>
 __device__ __forceinline__ void load_mod(Mod *s, const DevParams *dpp, int j)
 {
     if (threadIdx.x < sizeof(Mod) / 8) ((u64 *)s)[threadIdx.x] = ((const u64 *)&dpp->m[j])[threadIdx.x];
@@ -38,6 +37,8 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_cluster(const DevParams *dpp, EncodeA
 {
     constexpr int N = 1 << LOGN, T = N / 32, HALF = N / 2;
     extern __shared__ u64 sm[];
+    Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
+    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
     __shared__ Mod md;
     const u32 z = blockIdx.y, ib = blockIdx.x;
     const int L = dpp->L;
@@ -45,7 +46,9 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_cluster(const DevParams *dpp, EncodeA
     const u32 i = ib / g, b = ib % g, j = g * i + b, shift = (g * i) % HALF;
     const u32 c = a.chunk_cluster[z], k = a.chunk_k[z], size = a.size[c];
     const u64 row0 = a.row0[c];
-    load_mod<LOGN>(&md, dpp, L + 1);
+    load_mod(&md, dpp, L + 1);
+    load_tw_cache<LOGN>(twf, md.fwd);
+    load_tw_cache<LOGN>(twi, md.inv);
     const u64 t = md.p;
 #pragma unroll 4
     for (int u = 0; u < 32; u++) {
@@ -57,18 +60,20 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_cluster(const DevParams *dpp, EncodeA
         long v = (ue < size && cc < d) ? (long)a.emb[(row0 + ue) * d + cc] : 0;
         sm[pidx(dpp->slot_pos[s])] = v < 0 ? (u64)(v + (long)t) : (u64)v;
     }
-    ntt_inv<LOGN>(sm, md);
+    ntt_inv<LOGN>(sm, twi, md);
     u64 mc[32];
 #pragma unroll
     for (int u = 0; u < 32; u++) mc[u] = inv_finish(sm[pidx(threadIdx.x + T * u)], md);
     const u32 ts = a.ts, tiles = N / ts;
     for (int l = 0; l < L; l++) {
         __syncthreads();
-        load_mod<LOGN>(&md, dpp, l);
+        load_mod(&md, dpp, l);
+    load_tw_cache<LOGN>(twf, md.fwd);
+    load_tw_cache<LOGN>(twi, md.inv);
         const u64 q = md.p;
 #pragma unroll
         for (int u = 0; u < 32; u++) sm[pidx(threadIdx.x + T * u)] = mc[u] > (t - 1) / 2 ? q - (t - mc[u]) : mc[u];
-        ntt_fwd<LOGN>(sm, md);
+        ntt_fwd<LOGN>(sm, twf, md);
         u64 *base = a.ptxt + ((size_t)z * L + l) * tiles * ((size_t)dpad * ts);
 #pragma unroll 4
         for (int u = 0; u < 32; u++) {
@@ -85,11 +90,15 @@ __global__ void NTT_LB_WIDE(LOGN) k_export_cluster(const DevParams *dpp, Cluster
 {
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
+    Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
+    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
     __shared__ Mod md;
     const u32 ib = blockIdx.x, l = blockIdx.y, k = blockIdx.z;
     const int L = dpp->L;
     const u32 dpad = dpp->d_pad, ts = cs.ts, tiles = N / ts;
-    load_mod<LOGN>(&md, dpp, l);
+    load_mod(&md, dpp, l);
+    load_tw_cache<LOGN>(twf, md.fwd);
+    load_tw_cache<LOGN>(twi, md.inv);
     const u32 zz = cs.chunk0[cluster] + k;
     const u64 *base = cs.ptxt + ((size_t)zz * L + l) * tiles * ((size_t)dpad * ts);
 #pragma unroll 4
@@ -97,7 +106,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_export_cluster(const DevParams *dpp, Cluster
         const u32 e = threadIdx.x + T * u;
         sm[pidx(e)] = mont_redc(0, base[(size_t)(e / ts) * dpad * ts + (size_t)ib * ts + e % ts], md);
     }
-    ntt_inv<LOGN>(sm, md);
+    ntt_inv<LOGN>(sm, twi, md);
     u64 *d = out + (((size_t)k * dpad + ib) * L + l) * N;
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
@@ -114,11 +123,15 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_query(const DevParams *dpp, const int
 {
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
+    Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
+    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int L = dpp->L;
     const u32 d = dpp->d, dpad = dpp->d_pad;
-    load_mod<LOGN>(&md, dpp, L + 1);
+    load_mod(&md, dpp, L + 1);
+    load_tw_cache<LOGN>(twf, md.fwd);
+    load_tw_cache<LOGN>(twi, md.inv);
     const u64 t = md.p;
     const int8_t *qv = queries + (size_t)n * d;
 #pragma unroll 4
@@ -127,7 +140,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_query(const DevParams *dpp, const int
         long v = xx < d ? (long)qv[xx] : 0;
         sm[pidx(dpp->slot_pos[s])] = v < 0 ? (u64)(v + (long)t) : (u64)v;
     }
-    ntt_inv<LOGN>(sm, md);
+    ntt_inv<LOGN>(sm, twi, md);
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const u32 e = threadIdx.x + T * u;
@@ -138,20 +151,21 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_query(const DevParams *dpp, const int
 // sm <- NTT(a) * NTT(s) brought back by INTT: the negacyclic product a*s mod p.
 // sv holds NTT(s) for the thread's 32 positions.
 template <int LOGN>
-__device__ __forceinline__ void poly_times_secret(u64 *sm, const u64 sv[32], const Mod &md)
+__device__ __forceinline__ void poly_times_secret(u64 *sm, const u64 sv[32], const Mod &md, const Tw *twf,
+                                                  const Tw *twi)
 {
     constexpr int T = (1 << LOGN) / 32;
-    ntt_fwd<LOGN>(sm, md);
+    ntt_fwd<LOGN>(sm, twf, md);
 #pragma unroll
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
         sm[pidx(e)] = mulmod(fwd_finish(sm[pidx(e)], md), sv[u], md);
     }
-    ntt_inv<LOGN>(sm, md);
+    ntt_inv<LOGN>(sm, twi, md);
 }
 
 template <int LOGN>
-__device__ __forceinline__ void secret_ntt(u64 *sm, u64 sv[32], const int8_t *s, const Mod &md)
+__device__ __forceinline__ void secret_ntt(u64 *sm, u64 sv[32], const int8_t *s, const Mod &md, const Tw *twf)
 {
     constexpr int T = (1 << LOGN) / 32;
     __syncthreads();
@@ -161,7 +175,7 @@ __device__ __forceinline__ void secret_ntt(u64 *sm, u64 sv[32], const int8_t *s,
         const int v = s[e];
         sm[pidx(e)] = v < 0 ? md.p - 1 : (u64)v;
     }
-    ntt_fwd<LOGN>(sm, md);
+    ntt_fwd<LOGN>(sm, twf, md);
 #pragma unroll
     for (int u = 0; u < 32; u++) sv[u] = fwd_finish(sm[pidx(threadIdx.x + T * u)], md);
     __syncthreads();
@@ -174,20 +188,24 @@ __global__ void NTT_LB_WIDE(LOGN) k_encrypt(const DevParams *dpp, const int8_t *
 {
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
+    Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
+    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int l = blockIdx.y, L = dpp->L;
-    load_mod<LOGN>(&md, dpp, l);
+    load_mod(&md, dpp, l);
+    load_tw_cache<LOGN>(twf, md.fwd);
+    load_tw_cache<LOGN>(twi, md.inv);
     const u64 q = md.p;
     u64 sv[32];
-    secret_ntt<LOGN>(sm, sv, secret + (size_t)n * N, md);
+    secret_ntt<LOGN>(sm, sv, secret + (size_t)n * N, md, twf);
     const u64 *a = enc_a + ((size_t)n * L + l) * N;
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
         sm[pidx(e)] = a[e];
     }
-    poly_times_secret<LOGN>(sm, sv, md);
+    poly_times_secret<LOGN>(sm, sv, md, twf, twi);
     u64 *c0 = cts + ((size_t)n * 2 * L + l) * N, *c1 = cts + ((size_t)n * 2 * L + L + l) * N;
     const int8_t *ee = enc_e + (size_t)n * N;
     const u64 *mm = m + (size_t)n * N;
@@ -213,22 +231,26 @@ __global__ void NTT_LB_WIDE(LOGN) k_keygen(const DevParams *dpp, const int8_t *s
 {
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
+    Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
+    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int j = blockIdx.y, L = dpp->L;
     const int kk = blockIdx.z / L, i = blockIdx.z % L;
-    load_mod<LOGN>(&md, dpp, j);
+    load_mod(&md, dpp, j);
+    load_tw_cache<LOGN>(twf, md.fwd);
+    load_tw_cache<LOGN>(twi, md.inv);
     const u64 p = md.p;
     const int8_t *s = secret + (size_t)n * N;
     u64 sv[32];
-    secret_ntt<LOGN>(sm, sv, s, md);
+    secret_ntt<LOGN>(sm, sv, s, md, twf);
     const u64 *a = key_a + ((((size_t)n * 2 + kk) * L + i) * (L + 1) + j) * N;
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
         sm[pidx(e)] = a[e];
     }
-    poly_times_secret<LOGN>(sm, sv, md);
+    poly_times_secret<LOGN>(sm, sv, md, twf, twi);
     const int8_t *ee = key_e + (((size_t)n * 2 + kk) * L + i) * N;
     u64 *kb = keys + (((((size_t)n * 2 + kk) * L + i) * 2 + 0) * (L + 1) + j) * N;
     u64 *ka = keys + (((((size_t)n * 2 + kk) * L + i) * 2 + 1) * (L + 1) + j) * N;
@@ -261,20 +283,24 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_residues(const DevParams *dpp, const
 {
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
+    Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
+    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int l = blockIdx.y, L = dpp->L;
-    load_mod<LOGN>(&md, dpp, l);
+    load_mod(&md, dpp, l);
+    load_tw_cache<LOGN>(twf, md.fwd);
+    load_tw_cache<LOGN>(twi, md.inv);
     const u32 si = secret_index ? secret_index[n] : n;
     u64 sv[32];
-    secret_ntt<LOGN>(sm, sv, secret + (size_t)si * N, md);
+    secret_ntt<LOGN>(sm, sv, secret + (size_t)si * N, md, twf);
     const u64 *c0 = cts + ((size_t)n * 2 * L + l) * N, *c1 = cts + ((size_t)n * 2 * L + L + l) * N;
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
         sm[pidx(e)] = c1[e];
     }
-    poly_times_secret<LOGN>(sm, sv, md);
+    poly_times_secret<LOGN>(sm, sv, md, twf, twi);
     u64 *x = xs + ((size_t)n * L + l) * N;
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
@@ -292,10 +318,14 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u6
 {
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
+    Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
+    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int L = dpp->L;
-    load_mod<LOGN>(&md, dpp, L + 1);
+    load_mod(&md, dpp, L + 1);
+    load_tw_cache<LOGN>(twf, md.fwd);
+    load_tw_cache<LOGN>(twi, md.inv);
     const u64 t = md.p;
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
@@ -313,7 +343,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u6
         const u64 rnd = (u64)((frac + ((unsigned __int128)1 << 63)) >> 64);
         sm[pidx(e)] = (ipart + rnd) % t;
     }
-    ntt_fwd<LOGN>(sm, md);
+    ntt_fwd<LOGN>(sm, twf, md);
     for (int u = 0; u < 32; u++) {
         const int s = threadIdx.x + T * u;
         const u64 v = fwd_finish(sm[pidx(dpp->slot_pos[s])], md);
@@ -330,7 +360,7 @@ cudaError_t set_smem(K kernel, size_t bytes)
 template <int LOGN>
 cudaError_t set_attrs_logn()
 {
-    const size_t sb = smem_words(1 << LOGN) * 8;
+    const size_t sb = ntt_smem_words<LOGN>(2) * 8;
     cudaError_t e = cudaSuccess;
 #define SA(k) if (e == cudaSuccess) e = set_smem(k<LOGN>, sb)
     SA(k_encode_cluster);
@@ -354,7 +384,10 @@ cudaError_t set_attrs_logn()
     default: return cudaErrorInvalidValue;          \
     }
 
-static inline size_t smem_bytes(int log_n) { return smem_words(1 << log_n) * 8; }
+static inline size_t smem_bytes(int log_n)
+{
+    return log_n == 12 ? ntt_smem_words<12>(2) * 8 : log_n == 13 ? ntt_smem_words<13>(2) * 8 : ntt_smem_words<14>(2) * 8;
+}
 static inline int ntt_threads(int log_n) { return (1 << log_n) / 32; }
 
 static inline const DevParams *device_params_of(const DevParams &dp) { return dp.self; }

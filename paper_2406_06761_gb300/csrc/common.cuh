@@ -98,40 +98,37 @@ __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 p) { return a >= b ? a -
 
 // --------------------------------------------------------------------------- NTT
 // One CTA of N/32 threads transforms one polynomial held in shared memory.
-// Each pass loads groups of 2^R elements into registers, runs R butterfly
-// stages, and stores them back; three passes cover log2 N stages.  Shared
-// memory is padded by one word every 16 so that the stride-16 accesses of the
-// last pass do not collide in one bank.
+// Shared memory holds the N words with an XOR swizzle inside each 16-word row
+// (spos), so that every access pattern below is free of bank conflicts
+// without padding.
 //
-// Twiddles: stage s uses table entries [2^s, 2^(s+1)).  The entries of the
-// first two passes ([1, 2^(R0+R1)), at most 16 KB) are copied once per CTA
-// into shared memory; the last pass prefetches the 2^R - 1 entries of each
-// group from global memory before touching the group's data, so that their
-// latency overlaps the shared-memory loads instead of stalling each stage.
+// Passes: a remainder pass of R = log2 N mod 4 stages first (if any), then
+// radix-16 passes of 4 stages.  A pass loads groups of 2^R elements into
+// registers, runs its stages, and stores them back.  Every radix-16 pass runs
+// the same code with a run-time first stage S0, which keeps the instruction
+// footprint small.  Stage s uses twiddle entries [2^s, 2^(s+1)); those of all
+// passes but the last (entries below 2^(log2 N - 4), at most 16 KB) are
+// copied into a shared cache at the start of each transform, the last pass
+// reads its group's 15 twiddles from global memory before the group's data.
 
-__host__ __device__ constexpr int smem_words(int n) { return n + n / 16; }
-__device__ __forceinline__ int pidx(int x) { return x + (x >> 4); }
+__host__ __device__ constexpr int smem_words(int n) { return n; }
+__device__ __forceinline__ int spos(int x) { return x ^ ((x >> 4) & 15); }
 
 template <int LOGN>
 struct NttShape {
     static constexpr int N = 1 << LOGN;
-    static constexpr int T = N / 32;  // threads per CTA
-    // stage counts of the three passes
-    static constexpr int R0 = (LOGN == 12) ? 4 : 5;
-    static constexpr int R1 = (LOGN == 14) ? 5 : 4;
-    static constexpr int R2 = LOGN - R0 - R1;
-    // twiddle entries cached in shared memory: the first two passes
-    static constexpr int TW_CACHE = 1 << (R0 + R1);
-    // at most 128 registers a thread, so that two CTAs share an SM
-    static constexpr int MIN_BLOCKS = 65536 / (T * 128);
+    static constexpr int T = N / 32;           // threads per CTA
+    static constexpr int RR = LOGN % 4;        // stages of the remainder pass
+    static constexpr int TW_CACHE = 1 << (LOGN - 4);
+    // register budget: three CTAs share an SM at N = 8192 (85 registers)
+    static constexpr int MIN_BLOCKS = (LOGN == 12) ? 4 : (LOGN == 13 ? 3 : 1);
 };
 
-// Shared-memory words a kernel needs for one polynomial buffer plus the
-// twiddle caches of `dirs` directions (1 or 2).
+// Shared-memory words of a transform kernel: the polynomial and the cache.
 template <int LOGN>
-__host__ __device__ constexpr int ntt_smem_words(int dirs)
+__host__ __device__ constexpr int ntt_smem_words()
 {
-    return smem_words(1 << LOGN) + dirs * 2 * NttShape<LOGN>::TW_CACHE;
+    return smem_words(1 << LOGN) + 2 * NttShape<LOGN>::TW_CACHE;
 }
 
 __device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 p, u64 two_p)
@@ -149,7 +146,7 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 p, u6
     Y = shoup_mul(x - y + two_p, w, ws, p);
 }
 
-// Copy table entries [0, TW_CACHE) of one direction into shared memory.
+// Copy table entries [0, TW_CACHE) into the shared cache.
 template <int LOGN>
 __device__ __forceinline__ void load_tw_cache(Tw *dst, const Tw *__restrict__ src)
 {
@@ -157,21 +154,17 @@ __device__ __forceinline__ void load_tw_cache(Tw *dst, const Tw *__restrict__ sr
     for (int i = threadIdx.x; i < C; i += T) dst[i] = src[i];
 }
 
-// One butterfly stage ST (0-based inside the pass) on the 2^R registers v of
-// a group.  Stage s = S0 + ST pairs elements 2^(LOGN-1-s) apart (2^(R-1-ST)
-// apart inside the group); the block of element x is x >> (LOGN - s) and its
-// twiddle is table[2^s + block].  tws: the pass's twiddles, either the shared
-// cache indexed by table position (CACHED) or the group's prefetched list
-// indexed by (2^ST - 1 + block).  All register indices are compile-time
-// constants so that v stays in registers.
-template <int S0, int R, int ST, bool FWD, bool CACHED>
-__device__ __forceinline__ void ntt_stage(u64 *v, int hi, const Tw *tws, u64 p, u64 two_p)
+// Stage ST (0-based inside a pass of R stages) on the 2^R registers v of a
+// group; tw holds the group's twiddles in stage order (1, 2, 4, ... entries).
+// Stage ST pairs registers 2^(R-1-ST) apart; block b uses tw[2^ST - 1 + b].
+template <int R, int ST, bool FWD>
+__device__ __forceinline__ void group_stage(u64 *v, const Tw *tw, u64 p, u64 two_p)
 {
     constexpr int HD = 1 << (R - 1 - ST);
     constexpr int NB = 1 << ST;
 #pragma unroll
     for (int blk = 0; blk < NB; blk++) {
-        const Tw t = CACHED ? tws[(1 << (S0 + ST)) + ((hi << ST) | blk)] : tws[(NB - 1) + blk];
+        const Tw t = tw[(NB - 1) + blk];
 #pragma unroll
         for (int j = 0; j < HD; j++) {
             if (FWD) ct_bfly(v[blk * 2 * HD + j], v[blk * 2 * HD + j + HD], t.w, t.ws, p, two_p);
@@ -180,94 +173,103 @@ __device__ __forceinline__ void ntt_stage(u64 *v, int hi, const Tw *tws, u64 p, 
     }
 }
 
-template <int S0, int R, int ST, bool CACHED>
-__device__ __forceinline__ void ntt_stages_fwd(u64 *v, int hi, const Tw *tws, u64 p, u64 two_p)
+template <int R, int ST, bool FWD>
+__device__ __forceinline__ void group_stages(u64 *v, const Tw *tw, u64 p, u64 two_p)
 {
-    if constexpr (ST < R) {
-        ntt_stage<S0, R, ST, true, CACHED>(v, hi, tws, p, two_p);
-        ntt_stages_fwd<S0, R, ST + 1, CACHED>(v, hi, tws, p, two_p);
+    if constexpr (FWD) {
+        if constexpr (ST < R) {
+            group_stage<R, ST, true>(v, tw, p, two_p);
+            group_stages<R, ST + 1, true>(v, tw, p, two_p);
+        }
+    } else {
+        if constexpr (ST >= 0) {
+            group_stage<R, ST, false>(v, tw, p, two_p);
+            group_stages<R, ST - 1, false>(v, tw, p, two_p);
+        }
     }
 }
 
-template <int S0, int R, int ST, bool CACHED>
-__device__ __forceinline__ void ntt_stages_inv(u64 *v, int hi, const Tw *tws, u64 p, u64 two_p)
-{
-    if constexpr (ST >= 0) {
-        ntt_stage<S0, R, ST, false, CACHED>(v, hi, tws, p, two_p);
-        ntt_stages_inv<S0, R, ST - 1, CACHED>(v, hi, tws, p, two_p);
-    }
-}
-
-// Stages S0 .. S0+R-1 of the forward transform (FWD) or, in reverse order,
-// of the inverse transform, on groups of 2^R elements held in registers.
-// CACHED: twiddles from the shared cache `tcache`; otherwise from the global
-// table `tglob`, prefetched per group.
-template <int LOGN, int S0, int R, bool FWD, bool CACHED>
-__device__ __forceinline__ void ntt_pass(u64 *sm, const Tw *tcache, const Tw *__restrict__ tglob, u64 p, u64 two_p)
+// One pass: stages S0 .. S0+R-1 (forward) or in reverse order (inverse) on
+// all groups.  Group gi covers elements base + (k << BLO), k < 2^R, with
+// BLO = LOGN - R - S0 and base = (hi << (BLO + R)) | lo, hi = gi >> BLO,
+// lo = gi mod 2^BLO; the twiddle of its block at stage S0+st is entry
+// 2^(S0+st) + ((hi << st) | block), taken from `tws` (shared cache or global
+// table: a generic pointer).
+template <int LOGN, int R, bool FWD>
+__device__ __forceinline__ void ntt_pass(u64 *sm, int S0, const Tw *tws, u64 p, u64 two_p)
 {
     constexpr int T = NttShape<LOGN>::T;
     constexpr int G = 1 << R;
     constexpr int NG = 32 / G;
-    constexpr int BLO = LOGN - R - S0;
+    const int BLO = LOGN - R - S0;
     const int tid = threadIdx.x;
-#pragma unroll
+#pragma unroll 1
     for (int u = 0; u < NG; u++) {
         const int gi = tid + T * u;
         const int lo = gi & ((1 << BLO) - 1);
         const int hi = gi >> BLO;
         const int base = (hi << (BLO + R)) | lo;
-        Tw tw[CACHED ? 1 : G - 1];
-        if constexpr (!CACHED) {
+        Tw tw[G - 1];
 #pragma unroll
-            for (int st = 0, k = 0; st < R; st++)
+        for (int st = 0, k = 0; st < R; st++)
 #pragma unroll
-                for (int blk = 0; blk < (1 << st); blk++, k++) tw[k] = tglob[(1 << (S0 + st)) + ((hi << st) | blk)];
-        }
-        // element x = base + (k << BLO) lives at pidx(x) = pidx(base) + k*2^BLO + (k*2^BLO >> 4)
-        const int sb = pidx(base);
+            for (int blk = 0; blk < (1 << st); blk++, k++) tw[k] = tws[(1 << (S0 + st)) + ((hi << st) | blk)];
         u64 v[G];
 #pragma unroll
-        for (int k = 0; k < G; k++) v[k] = sm[sb + (k << BLO) + ((k << BLO) >> 4)];
-        if constexpr (FWD) ntt_stages_fwd<S0, R, 0, CACHED>(v, hi, CACHED ? tcache : tw, p, two_p);
-        else ntt_stages_inv<S0, R, R - 1, CACHED>(v, hi, CACHED ? tcache : tw, p, two_p);
+        for (int k = 0; k < G; k++) v[k] = sm[spos(base + (k << BLO))];
+        if constexpr (FWD) group_stages<R, 0, true>(v, tw, p, two_p);
+        else group_stages<R, R - 1, false>(v, tw, p, two_p);
 #pragma unroll
-        for (int k = 0; k < G; k++) sm[sb + (k << BLO) + ((k << BLO) >> 4)] = v[k];
+        for (int k = 0; k < G; k++) sm[spos(base + (k << BLO))] = v[k];
     }
 }
 
 // Forward negacyclic NTT in place: natural-order coefficients (any values
 // < 4p) -> evaluations at psi^(2*brv(i)+1) in bit-reversed position i, values
-// in [0, 4p).  tcache: this direction's shared twiddle cache (load_tw_cache,
-// made visible by a barrier before the call).  Ends with __syncthreads().
+// in [0, 4p).  cache: TW_CACHE shared entries (reloaded here).  Starts and
+// ends with __syncthreads().
 template <int LOGN>
-__device__ __forceinline__ void ntt_fwd(u64 *sm, const Tw *tcache, const Mod &md)
+__device__ __forceinline__ void ntt_fwd(u64 *sm, Tw *cache, const Mod &md)
 {
     using S = NttShape<LOGN>;
     const u64 p = md.p, two_p = md.two_p;
     __syncthreads();
-    ntt_pass<LOGN, 0, S::R0, true, true>(sm, tcache, md.fwd, p, two_p);
+    load_tw_cache<LOGN>(cache, md.fwd);
     __syncthreads();
-    ntt_pass<LOGN, S::R0, S::R1, true, true>(sm, tcache, md.fwd, p, two_p);
-    __syncthreads();
-    ntt_pass<LOGN, S::R0 + S::R1, S::R2, true, false>(sm, tcache, md.fwd, p, two_p);
+    if constexpr (S::RR > 0) {
+        ntt_pass<LOGN, S::RR, true>(sm, 0, cache, p, two_p);
+        __syncthreads();
+    }
+#pragma unroll 1
+    for (int s0 = S::RR; s0 < LOGN - 4; s0 += 4) {
+        ntt_pass<LOGN, 4, true>(sm, s0, cache, p, two_p);
+        __syncthreads();
+    }
+    ntt_pass<LOGN, 4, true>(sm, LOGN - 4, md.fwd, p, two_p);
     __syncthreads();
 }
 
 // Inverse: bit-reversed evaluations (values < 2p) -> natural-order
 // coefficients times N (values in [0, 2p)); callers scale by N^-1 with
-// inv_finish().  Ends with __syncthreads().
+// inv_finish().  Starts and ends with __syncthreads().
 template <int LOGN>
-__device__ __forceinline__ void ntt_inv(u64 *sm, const Tw *tcache, const Mod &md)
+__device__ __forceinline__ void ntt_inv(u64 *sm, Tw *cache, const Mod &md)
 {
     using S = NttShape<LOGN>;
     const u64 p = md.p, two_p = md.two_p;
     __syncthreads();
-    ntt_pass<LOGN, S::R0 + S::R1, S::R2, false, false>(sm, tcache, md.inv, p, two_p);
+    load_tw_cache<LOGN>(cache, md.inv);
+    ntt_pass<LOGN, 4, false>(sm, LOGN - 4, md.inv, p, two_p);
     __syncthreads();
-    ntt_pass<LOGN, S::R0, S::R1, false, true>(sm, tcache, md.inv, p, two_p);
-    __syncthreads();
-    ntt_pass<LOGN, 0, S::R0, false, true>(sm, tcache, md.inv, p, two_p);
-    __syncthreads();
+#pragma unroll 1
+    for (int s0 = LOGN - 8; s0 >= S::RR; s0 -= 4) {
+        ntt_pass<LOGN, 4, false>(sm, s0, cache, p, two_p);
+        __syncthreads();
+    }
+    if constexpr (S::RR > 0) {
+        ntt_pass<LOGN, S::RR, false>(sm, 0, cache, p, two_p);
+        __syncthreads();
+    }
 }
 
 // [0, 4p) -> [0, p)
@@ -290,7 +292,8 @@ __device__ __forceinline__ u32 galois_src(u32 j, u64 k, int log_n)
 // --------------------------------------------------------------------------- element IO
 // Elementwise sweeps use pairs: thread t owns elements 2(t + T*u) and
 // 2(t + T*u) + 1 for u < 16, so that global accesses are 16-byte and
-// coalesced.  Both elements of a pair sit in the same 16-word smem row.
+// coalesced.  Both elements of a pair sit in the same 16-word smem row, at
+// spos(e) and spos(e) ^ 1.
 template <int LOGN>
 __device__ __forceinline__ int pair_elem(int u)
 {
@@ -311,8 +314,8 @@ __device__ __forceinline__ void poly_load(u64 *sm, const u64 *g)
     for (int u = 0; u < 16; u++) {
         const int e = pair_elem<LOGN>(u);
         const ulonglong2 v = COHERENT ? ld2(g + e) : ldg2(g + e);
-        const int s = pidx(e);
+        const int s = spos(e);
         sm[s] = v.x;
-        sm[s + 1] = v.y;
+        sm[s ^ 1] = v.y;
     }
 }

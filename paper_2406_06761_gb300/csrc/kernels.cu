@@ -30,8 +30,8 @@ __device__ __forceinline__ u32 item_count(u32 n_max, const u32 *n_dev)
     return c < n_max ? c : n_max;
 }
 
-// Shared memory of the transform kernels: one padded polynomial buffer and the
-// twiddle caches of both directions.
+// Shared memory of the transform kernels: one polynomial buffer and the
+// twiddle cache.
 template <int LOGN>
 struct Smem {
     u64 *poly;
@@ -40,7 +40,7 @@ struct Smem {
     {
         poly = base;
         twf = reinterpret_cast<Tw *>(base + smem_words(1 << LOGN));
-        twi = twf + NttShape<LOGN>::TW_CACHE;
+        twi = twf;  // one cache, reloaded by every transform
     }
 };
 
@@ -62,15 +62,14 @@ __global__ void NTT_LB(LOGN) k_to_ntt(const DevParams *dpp, const u64 *const *sr
     if (x >= item_count(n_max, n_dev)) return;
     const u32 z = blockIdx.y;
     load_mod(&md, dpp, z % mod_cycle);
-    load_tw_cache<LOGN>(S.twf, md.fwd);
     const u64 *s = (src_ptrs ? src_ptrs[x] : src + x * src_stride) + (size_t)z * N;
     u64 *d = dst + x * dst_stride + (size_t)z * N;
     poly_load<LOGN>(S.poly, s);
     ntt_fwd<LOGN>(S.poly, S.twf, md);
 #pragma unroll 4
     for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = pidx(e);
-        u64 a = fwd_finish(S.poly[sp], md), b = fwd_finish(S.poly[sp + 1], md);
+        const int e = pair_elem<LOGN>(u), sp = spos(e);
+        u64 a = fwd_finish(S.poly[sp], md), b = fwd_finish(S.poly[sp ^ 1], md);
         if (mont) {
             a = mont_mul(a, md.r2, md);
             b = mont_mul(b, md.r2, md);
@@ -89,15 +88,14 @@ __global__ void NTT_LB(LOGN) k_from_ntt(const DevParams *dpp, const u64 *src, u6
     __shared__ Mod md;
     const u32 x = blockIdx.x, z = blockIdx.y;
     load_mod(&md, dpp, z % mod_cycle);
-    load_tw_cache<LOGN>(S.twi, md.inv);
     const u64 *s = src + ((size_t)x * polys + z) * N;
     u64 *d = dst + ((size_t)x * polys + z) * N;
     poly_load<LOGN>(S.poly, s);
     ntt_inv<LOGN>(S.poly, S.twi, md);
 #pragma unroll 4
     for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = pidx(e);
-        st2(d + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp + 1], md));
+        const int e = pair_elem<LOGN>(u), sp = spos(e);
+        st2(d + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp ^ 1], md));
     }
 }
 
@@ -114,7 +112,7 @@ __device__ __forceinline__ void permute_and_digit(const Smem<LOGN> &S, const Mod
 #pragma unroll 4
     for (int u = 0; u < 16; u++) {
         const int e = pair_elem<LOGN>(u);
-        st2(sc_cj + e, S.poly[pidx(galois_src(e, k, LOGN))], S.poly[pidx(galois_src(e + 1, k, LOGN))]);
+        st2(sc_cj + e, S.poly[spos(galois_src(e, k, LOGN))], S.poly[spos(galois_src(e + 1, k, LOGN))]);
     }
     if (c == 1) {
         __syncthreads();
@@ -122,8 +120,8 @@ __device__ __forceinline__ void permute_and_digit(const Smem<LOGN> &S, const Mod
         ntt_inv<LOGN>(S.poly, S.twi, md);
 #pragma unroll 4
         for (int u = 0; u < 16; u++) {
-            const int e = pair_elem<LOGN>(u), sp = pidx(e);
-            st2(dg_j + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp + 1], md));
+            const int e = pair_elem<LOGN>(u), sp = spos(e);
+            st2(dg_j + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp ^ 1], md));
         }
     }
 }
@@ -140,7 +138,6 @@ __global__ void NTT_LB(LOGN) k_ks_a(const DevParams *dpp, RotArgs a)
     if (x >= item_count(a.n_max, a.n_dev)) return;
     const int L = dpp->L, j = blockIdx.y % L, c = blockIdx.y / L;
     load_mod(&md, dpp, j);
-    if (c == 1) load_tw_cache<LOGN>(S.twi, md.inv);
     poly_load<LOGN>(S.poly, a.src + x * a.src_stride + ((size_t)c * L + j) * N);
     permute_and_digit<LOGN>(S, md, a.galois, c, a.sc + ((size_t)x * 2 * L + c * L + j) * N,
                             a.dg + ((size_t)x * L + j) * N);
@@ -163,8 +160,6 @@ __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
     if (x >= item_count(a.n_max, a.n_dev)) return;
     const int j = blockIdx.y, L = dpp->L;
     load_mod(&md, dpp, j);
-    load_tw_cache<LOGN>(S.twf, md.fwd);
-    if (j == L) load_tw_cache<LOGN>(S.twi, md.inv);
     const u64 *kx = a.key + (size_t)(a.key_map ? a.key_map[x] : x) * a.key_stride;
     u64 *dd = a.dd + ((size_t)x * (L + 1) + j) * L * N;
     const int last = (j == L - 1) ? L - 2 : L - 1;  // the last digit transformed here
@@ -177,8 +172,8 @@ __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
             u64 *di = dd + (size_t)i * N;
 #pragma unroll 4
             for (int u = 0; u < 16; u++) {
-                const int e = pair_elem<LOGN>(u), sp = pidx(e);
-                st2(di + e, S.poly[sp], S.poly[sp + 1]);  // lazy, < 4 p_j
+                const int e = pair_elem<LOGN>(u), sp = spos(e);
+                st2(di + e, S.poly[sp], S.poly[sp ^ 1]);  // lazy, < 4 p_j
             }
         }
     }
@@ -187,7 +182,7 @@ __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
     const u64 *sc1 = a.sc + ((size_t)x * 2 * L + L + j) * N;
 #pragma unroll 2
     for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = pidx(e);
+        const int e = pair_elem<LOGN>(u), sp = spos(e);
         u64 h0a = 0, l0a = 0, h0b = 0, l0b = 0, h1a = 0, l1a = 0, h1b = 0, l1b = 0;
         for (int i = 0; i < L; i++) {
             u64 da, db;
@@ -197,7 +192,7 @@ __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
                 db = t.y;
             } else if (i == last) {
                 da = S.poly[sp];
-                db = S.poly[sp + 1];
+                db = S.poly[sp ^ 1];
             } else {
                 const ulonglong2 t = ld2(dd + (size_t)i * N + e);
                 da = t.x;
@@ -221,8 +216,8 @@ __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
             ntt_inv<LOGN>(S.poly, S.twi, md);
 #pragma unroll 4
             for (int u = 0; u < 16; u++) {
-                const int e = pair_elem<LOGN>(u), sp = pidx(e);
-                st2(uc + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp + 1], md));
+                const int e = pair_elem<LOGN>(u), sp = spos(e);
+                st2(uc + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp ^ 1], md));
             }
         }
     }
@@ -245,17 +240,15 @@ __global__ void NTT_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
     if (x >= item_count(a.n_max, a.n_dev)) return;
     const int L = dpp->L, j = blockIdx.y % L, c = blockIdx.y / L;
     load_mod(&md, dpp, j);
-    load_tw_cache<LOGN>(S.twf, md.fwd);
-    if (a.next_galois && c == 1) load_tw_cache<LOGN>(S.twi, md.inv);
     const u64 q = md.p, P = dpp->m[L].p, half = (P - 1) / 2;
     const u64 pinv = dpp->pinv[j], pinv_s = dpp->pinv_s[j];
     const u64 *r = a.u + (((size_t)x * 2 + c) * (L + 1) + L) * N;
 #pragma unroll 4
     for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = pidx(e);
+        const int e = pair_elem<LOGN>(u), sp = spos(e);
         const ulonglong2 rv = ldg2(r + e);
         S.poly[sp] = rv.x > half ? q - (P - rv.x) : rv.x;  // r_c mod q_j, < 4q
-        S.poly[sp + 1] = rv.y > half ? q - (P - rv.y) : rv.y;
+        S.poly[sp ^ 1] = rv.y > half ? q - (P - rv.y) : rv.y;
     }
     ntt_fwd<LOGN>(S.poly, S.twf, md);
     const u64 *uj = a.u + (((size_t)x * 2 + c) * (L + 1) + j) * N;
@@ -264,10 +257,10 @@ __global__ void NTT_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
     u64 *dst = a.dst + x * a.dst_stride + ((size_t)c * L + j) * N;
 #pragma unroll 4
     for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = pidx(e);
+        const int e = pair_elem<LOGN>(u), sp = spos(e);
         const ulonglong2 uv = ldg2(uj + e);
         u64 v0 = csub(shoup_mul(uv.x + q - fwd_finish(S.poly[sp], md), pinv, pinv_s, q), q);
-        u64 v1 = csub(shoup_mul(uv.y + q - fwd_finish(S.poly[sp + 1], md), pinv, pinv_s, q), q);
+        u64 v1 = csub(shoup_mul(uv.y + q - fwd_finish(S.poly[sp ^ 1], md), pinv, pinv_s, q), q);
         if (c == 0) {
             const ulonglong2 s0 = ld2(sc_cj + e);
             v0 = addmod(v0, s0.x, q);
@@ -280,7 +273,7 @@ __global__ void NTT_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
         }
         st2(dst + e, v0, v1);
         S.poly[sp] = v0;  // same thread, same positions: the output replaces NTT(r)
-        S.poly[sp + 1] = v1;
+        S.poly[sp ^ 1] = v1;
     }
     if (a.next_galois)
         permute_and_digit<LOGN>(S, md, a.next_galois, c, sc_cj, a.dg + ((size_t)x * L + j) * N);
@@ -369,15 +362,14 @@ __global__ void NTT_LB(LOGN) k_output(const DevParams *dpp, WavePlan wp, const u
     const int L = dpp->L;
     const int z = blockIdx.y, l = z % L;
     load_mod(&md, dpp, l);
-    load_tw_cache<LOGN>(S.twi, md.inv);
     const u64 *s = S_ + p * S_stride + (size_t)z * N;
     u64 *d = wp.dst_out[wp.pair_pos[p]] + (size_t)wp.pair_k[p] * 2 * L * N + (size_t)z * N;
     poly_load<LOGN>(S.poly, s);
     ntt_inv<LOGN>(S.poly, S.twi, md);
 #pragma unroll 4
     for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = pidx(e);
-        st2(d + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp + 1], md));
+        const int e = pair_elem<LOGN>(u), sp = spos(e);
+        st2(d + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp ^ 1], md));
     }
 }
 
@@ -501,7 +493,7 @@ cudaError_t set_smem(K kernel, size_t bytes)
 template <int LOGN>
 cudaError_t set_attrs_logn()
 {
-    const size_t sb = ntt_smem_words<LOGN>(2) * 8;
+    const size_t sb = ntt_smem_words<LOGN>() * 8;
     cudaError_t e = cudaSuccess;
 #define SA(k) if (e == cudaSuccess) e = set_smem(k<LOGN>, sb)
     SA(k_to_ntt);
@@ -524,7 +516,7 @@ cudaError_t set_attrs_logn()
     default: return cudaErrorInvalidValue;          \
     }
 
-#define SMEM(LG) (ntt_smem_words<LG>(2) * 8)
+#define SMEM(LG) (ntt_smem_words<LG>() * 8)
 static inline int ntt_threads(int log_n) { return (1 << log_n) / 32; }
 
 cudaError_t set_client_kernel_attributes(int log_n);

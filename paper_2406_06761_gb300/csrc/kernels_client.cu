@@ -38,7 +38,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_cluster(const DevParams *dpp, EncodeA
     constexpr int N = 1 << LOGN, T = N / 32, HALF = N / 2;
     extern __shared__ u64 sm[];
     Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
-    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
+    Tw *twi = twf;  // one cache, reloaded by every transform
     __shared__ Mod md;
     const u32 z = blockIdx.y, ib = blockIdx.x;
     const int L = dpp->L;
@@ -47,8 +47,6 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_cluster(const DevParams *dpp, EncodeA
     const u32 c = a.chunk_cluster[z], k = a.chunk_k[z], size = a.size[c];
     const u64 row0 = a.row0[c];
     load_mod(&md, dpp, L + 1);
-    load_tw_cache<LOGN>(twf, md.fwd);
-    load_tw_cache<LOGN>(twi, md.inv);
     const u64 t = md.p;
 #pragma unroll 4
     for (int u = 0; u < 32; u++) {
@@ -58,27 +56,25 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_cluster(const DevParams *dpp, EncodeA
         const u32 xx = src % dpad, cc = (xx + j) % dpad;
         const u64 ue = (u64)k * N + src;
         long v = (ue < size && cc < d) ? (long)a.emb[(row0 + ue) * d + cc] : 0;
-        sm[pidx(dpp->slot_pos[s])] = v < 0 ? (u64)(v + (long)t) : (u64)v;
+        sm[spos(dpp->slot_pos[s])] = v < 0 ? (u64)(v + (long)t) : (u64)v;
     }
     ntt_inv<LOGN>(sm, twi, md);
     u64 mc[32];
 #pragma unroll
-    for (int u = 0; u < 32; u++) mc[u] = inv_finish(sm[pidx(threadIdx.x + T * u)], md);
+    for (int u = 0; u < 32; u++) mc[u] = inv_finish(sm[spos(threadIdx.x + T * u)], md);
     const u32 ts = a.ts, tiles = N / ts;
     for (int l = 0; l < L; l++) {
         __syncthreads();
         load_mod(&md, dpp, l);
-    load_tw_cache<LOGN>(twf, md.fwd);
-    load_tw_cache<LOGN>(twi, md.inv);
         const u64 q = md.p;
 #pragma unroll
-        for (int u = 0; u < 32; u++) sm[pidx(threadIdx.x + T * u)] = mc[u] > (t - 1) / 2 ? q - (t - mc[u]) : mc[u];
+        for (int u = 0; u < 32; u++) sm[spos(threadIdx.x + T * u)] = mc[u] > (t - 1) / 2 ? q - (t - mc[u]) : mc[u];
         ntt_fwd<LOGN>(sm, twf, md);
         u64 *base = a.ptxt + ((size_t)z * L + l) * tiles * ((size_t)dpad * ts);
 #pragma unroll 4
         for (int u = 0; u < 32; u++) {
             const u32 e = threadIdx.x + T * u;
-            u64 v = mont_mul(fwd_finish(sm[pidx(e)], md), md.r2, md);
+            u64 v = mont_mul(fwd_finish(sm[spos(e)], md), md.r2, md);
             base[(size_t)(e / ts) * dpad * ts + (size_t)ib * ts + e % ts] = v;
         }
     }
@@ -91,27 +87,25 @@ __global__ void NTT_LB_WIDE(LOGN) k_export_cluster(const DevParams *dpp, Cluster
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
     Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
-    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
+    Tw *twi = twf;  // one cache, reloaded by every transform
     __shared__ Mod md;
     const u32 ib = blockIdx.x, l = blockIdx.y, k = blockIdx.z;
     const int L = dpp->L;
     const u32 dpad = dpp->d_pad, ts = cs.ts, tiles = N / ts;
     load_mod(&md, dpp, l);
-    load_tw_cache<LOGN>(twf, md.fwd);
-    load_tw_cache<LOGN>(twi, md.inv);
     const u32 zz = cs.chunk0[cluster] + k;
     const u64 *base = cs.ptxt + ((size_t)zz * L + l) * tiles * ((size_t)dpad * ts);
 #pragma unroll 4
     for (int u = 0; u < 32; u++) {
         const u32 e = threadIdx.x + T * u;
-        sm[pidx(e)] = mont_redc(0, base[(size_t)(e / ts) * dpad * ts + (size_t)ib * ts + e % ts], md);
+        sm[spos(e)] = mont_redc(0, base[(size_t)(e / ts) * dpad * ts + (size_t)ib * ts + e % ts], md);
     }
     ntt_inv<LOGN>(sm, twi, md);
     u64 *d = out + (((size_t)k * dpad + ib) * L + l) * N;
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const u32 e = threadIdx.x + T * u;
-        d[e] = inv_finish(sm[pidx(e)], md);
+        d[e] = inv_finish(sm[spos(e)], md);
     }
 }
 
@@ -124,48 +118,46 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_query(const DevParams *dpp, const int
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
     Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
-    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
+    Tw *twi = twf;  // one cache, reloaded by every transform
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int L = dpp->L;
     const u32 d = dpp->d, dpad = dpp->d_pad;
     load_mod(&md, dpp, L + 1);
-    load_tw_cache<LOGN>(twf, md.fwd);
-    load_tw_cache<LOGN>(twi, md.inv);
     const u64 t = md.p;
     const int8_t *qv = queries + (size_t)n * d;
 #pragma unroll 4
     for (int u = 0; u < 32; u++) {
         const u32 s = threadIdx.x + T * u, xx = s % dpad;
         long v = xx < d ? (long)qv[xx] : 0;
-        sm[pidx(dpp->slot_pos[s])] = v < 0 ? (u64)(v + (long)t) : (u64)v;
+        sm[spos(dpp->slot_pos[s])] = v < 0 ? (u64)(v + (long)t) : (u64)v;
     }
     ntt_inv<LOGN>(sm, twi, md);
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const u32 e = threadIdx.x + T * u;
-        m_out[(size_t)n * N + e] = inv_finish(sm[pidx(e)], md);
+        m_out[(size_t)n * N + e] = inv_finish(sm[spos(e)], md);
     }
 }
 
 // sm <- NTT(a) * NTT(s) brought back by INTT: the negacyclic product a*s mod p.
 // sv holds NTT(s) for the thread's 32 positions.
 template <int LOGN>
-__device__ __forceinline__ void poly_times_secret(u64 *sm, const u64 sv[32], const Mod &md, const Tw *twf,
-                                                  const Tw *twi)
+__device__ __forceinline__ void poly_times_secret(u64 *sm, const u64 sv[32], const Mod &md, Tw *twf,
+                                                  Tw *twi)
 {
     constexpr int T = (1 << LOGN) / 32;
     ntt_fwd<LOGN>(sm, twf, md);
 #pragma unroll
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
-        sm[pidx(e)] = mulmod(fwd_finish(sm[pidx(e)], md), sv[u], md);
+        sm[spos(e)] = mulmod(fwd_finish(sm[spos(e)], md), sv[u], md);
     }
     ntt_inv<LOGN>(sm, twi, md);
 }
 
 template <int LOGN>
-__device__ __forceinline__ void secret_ntt(u64 *sm, u64 sv[32], const int8_t *s, const Mod &md, const Tw *twf)
+__device__ __forceinline__ void secret_ntt(u64 *sm, u64 sv[32], const int8_t *s, const Mod &md, Tw *twf)
 {
     constexpr int T = (1 << LOGN) / 32;
     __syncthreads();
@@ -173,11 +165,11 @@ __device__ __forceinline__ void secret_ntt(u64 *sm, u64 sv[32], const int8_t *s,
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
         const int v = s[e];
-        sm[pidx(e)] = v < 0 ? md.p - 1 : (u64)v;
+        sm[spos(e)] = v < 0 ? md.p - 1 : (u64)v;
     }
     ntt_fwd<LOGN>(sm, twf, md);
 #pragma unroll
-    for (int u = 0; u < 32; u++) sv[u] = fwd_finish(sm[pidx(threadIdx.x + T * u)], md);
+    for (int u = 0; u < 32; u++) sv[u] = fwd_finish(sm[spos(threadIdx.x + T * u)], md);
     __syncthreads();
 }
 
@@ -189,13 +181,11 @@ __global__ void NTT_LB_WIDE(LOGN) k_encrypt(const DevParams *dpp, const int8_t *
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
     Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
-    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
+    Tw *twi = twf;  // one cache, reloaded by every transform
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int l = blockIdx.y, L = dpp->L;
     load_mod(&md, dpp, l);
-    load_tw_cache<LOGN>(twf, md.fwd);
-    load_tw_cache<LOGN>(twi, md.inv);
     const u64 q = md.p;
     u64 sv[32];
     secret_ntt<LOGN>(sm, sv, secret + (size_t)n * N, md, twf);
@@ -203,7 +193,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_encrypt(const DevParams *dpp, const int8_t *
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
-        sm[pidx(e)] = a[e];
+        sm[spos(e)] = a[e];
     }
     poly_times_secret<LOGN>(sm, sv, md, twf, twi);
     u64 *c0 = cts + ((size_t)n * 2 * L + l) * N, *c1 = cts + ((size_t)n * 2 * L + L + l) * N;
@@ -213,7 +203,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_encrypt(const DevParams *dpp, const int8_t *
 #pragma unroll 4
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
-        const u64 as = inv_finish(sm[pidx(e)], md);
+        const u64 as = inv_finish(sm[spos(e)], md);
         const int ev = ee[e];
         u64 v = submod(ev < 0 ? q - (u64)(-ev) : (u64)ev, as, q);
         v = addmod(v, csub(shoup_mul(mm[e], dl, dls, q), q), q);
@@ -232,14 +222,12 @@ __global__ void NTT_LB_WIDE(LOGN) k_keygen(const DevParams *dpp, const int8_t *s
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
     Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
-    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
+    Tw *twi = twf;  // one cache, reloaded by every transform
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int j = blockIdx.y, L = dpp->L;
     const int kk = blockIdx.z / L, i = blockIdx.z % L;
     load_mod(&md, dpp, j);
-    load_tw_cache<LOGN>(twf, md.fwd);
-    load_tw_cache<LOGN>(twi, md.inv);
     const u64 p = md.p;
     const int8_t *s = secret + (size_t)n * N;
     u64 sv[32];
@@ -248,7 +236,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_keygen(const DevParams *dpp, const int8_t *s
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
-        sm[pidx(e)] = a[e];
+        sm[spos(e)] = a[e];
     }
     poly_times_secret<LOGN>(sm, sv, md, twf, twi);
     const int8_t *ee = key_e + (((size_t)n * 2 + kk) * L + i) * N;
@@ -259,7 +247,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_keygen(const DevParams *dpp, const int8_t *s
 #pragma unroll 4
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
-        const u64 as = inv_finish(sm[pidx(e)], md);
+        const u64 as = inv_finish(sm[spos(e)], md);
         const int ev = ee[e];
         u64 v = submod(ev < 0 ? p - (u64)(-ev) : (u64)ev, as, p);
         if (i == j) {
@@ -284,13 +272,11 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_residues(const DevParams *dpp, const
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
     Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
-    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
+    Tw *twi = twf;  // one cache, reloaded by every transform
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int l = blockIdx.y, L = dpp->L;
     load_mod(&md, dpp, l);
-    load_tw_cache<LOGN>(twf, md.fwd);
-    load_tw_cache<LOGN>(twi, md.inv);
     const u32 si = secret_index ? secret_index[n] : n;
     u64 sv[32];
     secret_ntt<LOGN>(sm, sv, secret + (size_t)si * N, md, twf);
@@ -298,14 +284,14 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_residues(const DevParams *dpp, const
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
-        sm[pidx(e)] = c1[e];
+        sm[spos(e)] = c1[e];
     }
     poly_times_secret<LOGN>(sm, sv, md, twf, twi);
     u64 *x = xs + ((size_t)n * L + l) * N;
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
-        x[e] = addmod(inv_finish(sm[pidx(e)], md), c0[e], md.p);
+        x[e] = addmod(inv_finish(sm[spos(e)], md), c0[e], md.p);
     }
 }
 
@@ -319,13 +305,11 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u6
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
     Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
-    Tw *twi = twf + NttShape<LOGN>::TW_CACHE;
+    Tw *twi = twf;  // one cache, reloaded by every transform
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int L = dpp->L;
     load_mod(&md, dpp, L + 1);
-    load_tw_cache<LOGN>(twf, md.fwd);
-    load_tw_cache<LOGN>(twi, md.inv);
     const u64 t = md.p;
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
@@ -341,12 +325,12 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u6
             frac += (u64)(((unsigned __int128)rem << 64) / q);
         }
         const u64 rnd = (u64)((frac + ((unsigned __int128)1 << 63)) >> 64);
-        sm[pidx(e)] = (ipart + rnd) % t;
+        sm[spos(e)] = (ipart + rnd) % t;
     }
     ntt_fwd<LOGN>(sm, twf, md);
     for (int u = 0; u < 32; u++) {
         const int s = threadIdx.x + T * u;
-        const u64 v = fwd_finish(sm[pidx(dpp->slot_pos[s])], md);
+        const u64 v = fwd_finish(sm[spos(dpp->slot_pos[s])], md);
         scores[(size_t)n * N + s] = v > t / 2 ? (int64_t)v - (int64_t)t : (int64_t)v;
     }
 }
@@ -360,7 +344,7 @@ cudaError_t set_smem(K kernel, size_t bytes)
 template <int LOGN>
 cudaError_t set_attrs_logn()
 {
-    const size_t sb = ntt_smem_words<LOGN>(2) * 8;
+    const size_t sb = ntt_smem_words<LOGN>() * 8;
     cudaError_t e = cudaSuccess;
 #define SA(k) if (e == cudaSuccess) e = set_smem(k<LOGN>, sb)
     SA(k_encode_cluster);
@@ -386,7 +370,7 @@ cudaError_t set_attrs_logn()
 
 static inline size_t smem_bytes(int log_n)
 {
-    return log_n == 12 ? ntt_smem_words<12>(2) * 8 : log_n == 13 ? ntt_smem_words<13>(2) * 8 : ntt_smem_words<14>(2) * 8;
+    return log_n == 12 ? ntt_smem_words<12>() * 8 : log_n == 13 ? ntt_smem_words<13>() * 8 : ntt_smem_words<14>() * 8;
 }
 static inline int ntt_threads(int log_n) { return (1 << log_n) / 32; }
 

@@ -157,6 +157,24 @@ int wally_eval_batch_host(wally_ctx *ctx, uint32_t n, const uint32_t *cluster_id
 int wally_rotate(wally_ctx *ctx, uint32_t n, uint64_t galois_elt, const uint64_t *cts, const uint64_t *keys,
                  uint64_t *out, void *stream);
 
+/* wally_rotate without any device allocation (the paper has no counterpart:
+ * this is a service for callers, not a step of the method).  For callers
+ * that must not call cudaMalloc/cudaFree at this point -- a serving thread
+ * that cannot take the device-wide synchronisation those calls cause while
+ * other streams run, or a process whose framework allocator already owns all
+ * device memory.  Same arguments, layouts and results as wally_rotate.
+ * Its scratch is one static device array of WALLY_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library keeps until exit; n is limited to
+ *   WALLY_NOALLOC_SCRATCH_BYTES / (8 N (7L + 2 + 3L(L+1)))
+ * ciphertexts (4 at N = 8192, L = 3); larger n returns WALLY_EINVAL.  The
+ * first call on a device looks up the array's device address (set-up), so
+ * make it before any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (other streams, other contexts on the device) race
+ * and must be serialised by the caller.  Asynchronous on `stream`. */
+#define WALLY_NOALLOC_SCRATCH_BYTES (16u << 20)
+int wally_rotate_noalloc(wally_ctx *ctx, uint32_t n, uint64_t galois_elt, const uint64_t *cts,
+                         const uint64_t *keys, uint64_t *out, void *stream);
+
 /* Wait for `stream` and report the first device-side error recorded since
  * the previous wally_sync (and clear it). */
 int wally_sync(wally_ctx *ctx, void *stream);

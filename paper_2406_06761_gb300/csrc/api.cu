@@ -11,6 +11,7 @@
 #include "../../include/wally.h"
 #include "host_nt.hpp"
 #include "kernels.hpp"
+#include "ctx_access.hpp"
 
 using namespace wally;
 
@@ -393,6 +394,20 @@ int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t s
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
+
+namespace wally {
+bool ctx_view(const wally_ctx *c, const DevParams **dp, int *device, uint32_t *n, uint32_t *L)
+{
+    if (!c) return false;
+    *dp = &c->dp;
+    *device = c->device;
+    *n = c->N;
+    *L = c->L;
+    return true;
+}
+
+int ctx_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace wally
 
 extern "C" {
 

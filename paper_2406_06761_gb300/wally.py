@@ -65,6 +65,7 @@ SIGNATURES = {
     "wally_eval_batch": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "wally_eval_batch_host": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "wally_rotate": (ctypes.c_int, [_vp, _u32, _u64, _vp, _vp, _vp, _vp]),
+    "wally_rotate_noalloc": (ctypes.c_int, [_vp, _u32, _u64, _vp, _vp, _vp, _vp]),
     "wally_sync": (ctypes.c_int, [_vp, _vp]),
     "wally_keygen": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "wally_encrypt_query": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -196,6 +197,12 @@ def wally_eval_batch_host(ctx: int, n: int, cluster_ids, cts, galois_keys, input
 def wally_rotate(ctx: int, n: int, galois_elt: int, cts, keys, out, stream=None) -> None:
     _require_cuda(cts, keys, out)
     _check(load().wally_rotate(ctx, n, galois_elt, _ptr(cts), _ptr(keys), _ptr(out), _stream(stream)))
+
+
+def wally_rotate_noalloc(ctx: int, n: int, galois_elt: int, cts, keys, out, stream=None) -> None:
+    """wally_rotate without device allocation (fixed static scratch; small n)."""
+    _require_cuda(cts, keys, out)
+    _check(load().wally_rotate_noalloc(ctx, n, galois_elt, _ptr(cts), _ptr(keys), _ptr(out), _stream(stream)))
 
 
 def wally_sync(ctx: int, stream=None) -> None:

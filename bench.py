@@ -197,6 +197,7 @@ def main():
     import torch.distributed as dist
 
     from paper_2406_06761_gb300 import harness as H
+    from paper_2406_06761_gb300 import multigpu as M
     from paper_2406_06761_gb300 import wally as Wl
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -255,8 +256,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     Wl.wally_profile_enable(wl.ctx.ptr, True)
-    if world > 1:
-        dist.barrier()
+    M.barrier()
     torch.cuda.synchronize(dev)
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
@@ -266,18 +266,14 @@ def main():
         step(marks)
     end.record(stream)
     torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    M.barrier()
     Wl.wally_sync(wl.ctx.ptr)
     ms_total = start.elapsed_time(end)
     prof = Wl.wally_profile_read(wl.ctx.ptr)
     Wl.wally_profile_enable(wl.ctx.ptr, False)
     clk = clocks.stop()
     ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = M.max_over_ranks(ms_step, device=dev)
     value = world * n / (ms_step / 1e3)
 
     # latency: completion time of each query's sub-batch within its step

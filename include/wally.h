@@ -142,6 +142,18 @@ int wally_eval_batch(wally_ctx *ctx, uint32_t n, const uint32_t *cluster_ids, co
                      const uint64_t *galois_keys, const uint32_t *input_index, const uint64_t *out_offsets,
                      uint64_t *out, void *stream);
 
+/* wally_eval_batch on one of WALLY_MAX_LANES independent workspaces
+ * ("lanes") of the context.  Lanes share the context's tables and resident
+ * clusters, so calls on different lanes may overlap on different streams
+ * (continuous batching: a new wave is admitted on a free lane while others
+ * are still running).  Calls on the same lane must not overlap.
+ * wally_eval_batch is lane 0.  Each lane allocates its own workspace on first
+ * use. */
+#define WALLY_MAX_LANES 4
+int wally_eval_batch_lane(wally_ctx *ctx, uint32_t lane, uint32_t n, const uint32_t *cluster_ids,
+                          const uint64_t *cts, const uint64_t *galois_keys, const uint32_t *input_index,
+                          const uint64_t *out_offsets, uint64_t *out, void *stream);
+
 /* wally_eval_batch with HOST buffers (same layouts; cluster_ids, input_index,
  * out_offsets host arrays too).  Copies each wave's inputs to the device,
  * evaluates, and copies the results back; returns when `out` is filled.

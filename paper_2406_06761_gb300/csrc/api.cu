@@ -115,6 +115,37 @@ struct EventProfiler : Profiler {
     }
 };
 
+// One independent evaluation workspace.  Lanes of a context share its
+// read-only tables and cluster store, so waves on different lanes (different
+// streams) may run concurrently.
+struct Lane {
+    uint32_t ws_wave = 0, ws_mmax = 0;
+    DevBuf<u64> keysN, ctp, T, S, sc, dg, u, dd;
+    DevBuf<u32> plan_u32;
+    DevBuf<void *> plan_ptr;
+    WavePlan wp{};
+    // batch grouping
+    DevBuf<u32> counts, cstart, fill, sorted_q;
+    void release()
+    {
+        keysN.release();
+        ctp.release();
+        T.release();
+        S.release();
+        sc.release();
+        dg.release();
+        u.release();
+        dd.release();
+        plan_u32.release();
+        plan_ptr.release();
+        counts.release();
+        cstart.release();
+        fill.release();
+        sorted_q.release();
+        ws_wave = ws_mmax = 0;
+    }
+};
+
 }  // namespace
 
 struct wally_ctx {
@@ -137,14 +168,8 @@ struct wally_ctx {
     DevBuf<u64> ptxt;
     DevBuf<u32> d_chunks, d_chunk0;
 
-    // wave workspace
-    uint32_t ws_wave = 0, ws_mmax = 0;
-    DevBuf<u64> keysN, ctp, T, S, sc, dg, u, dd;
-    DevBuf<u32> plan_u32;
-    DevBuf<void *> plan_ptr;
-    WavePlan wp{};
-    // batch grouping
-    DevBuf<u32> counts, cstart, fill, sorted_q;
+    // evaluation workspaces
+    Lane lanes[WALLY_MAX_LANES];
     // host-buffer path staging
     DevBuf<u64> stage_ct[2], stage_key[2], stage_out[2];
     DevBuf<u32> stage_cluster[2];
@@ -257,33 +282,33 @@ uint64_t inv_mod_2n(uint64_t k, uint64_t two_n)
 }
 
 // Wave workspace for W queries and up to W * m_max (query, chunk) pairs.
-int ensure_workspace(wally_ctx *c, uint32_t W, uint32_t m_max)
+int ensure_workspace(wally_ctx *c, Lane &ln, uint32_t W, uint32_t m_max)
 {
-    if (c->ws_wave >= W && c->ws_mmax >= m_max && c->keysN.p) return WALLY_OK;
-    W = std::max(W, c->ws_wave);
-    m_max = std::max(m_max, std::max(c->ws_mmax, 1u));
+    if (ln.ws_wave >= W && ln.ws_mmax >= m_max && ln.keysN.p) return WALLY_OK;
+    W = std::max(W, ln.ws_wave);
+    m_max = std::max(m_max, std::max(ln.ws_mmax, 1u));
     const size_t ctw = c->ctw(), keysw = c->keysw(), N = c->N, L = c->L;
     const size_t pairs = (size_t)W * m_max;
-    c->keysN.release();
-    c->ctp.release();
-    c->T.release();
-    c->S.release();
-    c->sc.release();
-    c->dg.release();
-    c->u.release();
-    c->dd.release();
+    ln.keysN.release();
+    ln.ctp.release();
+    ln.T.release();
+    ln.S.release();
+    ln.sc.release();
+    ln.dg.release();
+    ln.u.release();
+    ln.dd.release();
     const size_t items = std::max(pairs, (size_t)W);
-    if (c->keysN.ensure(W * keysw) != cudaSuccess || c->ctp.ensure(W * (size_t)c->g * ctw) != cudaSuccess ||
-        c->T.ensure(pairs * c->h * ctw) != cudaSuccess || c->S.ensure(items * ctw) != cudaSuccess ||
-        c->sc.ensure(items * ctw) != cudaSuccess || c->dg.ensure(items * L * N) != cudaSuccess ||
-        c->u.ensure(items * 2 * (L + 1) * N) != cudaSuccess || c->dd.ensure(items * (L + 1) * L * N) != cudaSuccess)
+    if (ln.keysN.ensure(W * keysw) != cudaSuccess || ln.ctp.ensure(W * (size_t)c->g * ctw) != cudaSuccess ||
+        ln.T.ensure(pairs * c->h * ctw) != cudaSuccess || ln.S.ensure(items * ctw) != cudaSuccess ||
+        ln.sc.ensure(items * ctw) != cudaSuccess || ln.dg.ensure(items * L * N) != cudaSuccess ||
+        ln.u.ensure(items * 2 * (L + 1) * N) != cudaSuccess || ln.dd.ensure(items * (L + 1) * L * N) != cudaSuccess)
         return fail(WALLY_ENOMEM, "cannot allocate the wave workspace (%u queries, %u chunks max)", W, m_max);
     // plan arrays: counts[4] | cluster[W] | pair_pos[P] | pair_k[P] | pair_off[W+1] | seg x3 [W]
     const size_t n32 = 4 + W + 2 * pairs + (W + 1) + 3 * (size_t)W;
-    if (c->plan_u32.ensure(n32) != cudaSuccess || c->plan_ptr.ensure(3 * (size_t)W) != cudaSuccess)
+    if (ln.plan_u32.ensure(n32) != cudaSuccess || ln.plan_ptr.ensure(3 * (size_t)W) != cudaSuccess)
         return fail(WALLY_ENOMEM, "cannot allocate the wave plan");
-    u32 *b = c->plan_u32.p;
-    WavePlan &wp = c->wp;
+    u32 *b = ln.plan_u32.p;
+    WavePlan &wp = ln.wp;
     wp.counts = b;
     b += 4;
     wp.cluster = b;
@@ -299,12 +324,12 @@ int ensure_workspace(wally_ctx *c, uint32_t W, uint32_t m_max)
     wp.seg_begin = b;
     b += W;
     wp.seg_end = b;
-    void **pp = c->plan_ptr.p;
+    void **pp = ln.plan_ptr.p;
     wp.src_ct = (const u64 **)pp;
     wp.src_key = (const u64 **)(pp + W);
     wp.dst_out = (u64 **)(pp + 2 * (size_t)W);
-    c->ws_wave = W;
-    c->ws_mmax = m_max;
+    ln.ws_wave = W;
+    ln.ws_mmax = m_max;
     return WALLY_OK;
 }
 
@@ -318,38 +343,38 @@ ClusterStore cluster_store(const wally_ctx *c)
     return cs;
 }
 
-RotArgs rot_args(wally_ctx *c)
+RotArgs rot_args(Lane &ln)
 {
     RotArgs a;
     memset(&a, 0, sizeof(a));
-    a.sc = c->sc.p;
-    a.dg = c->dg.p;
-    a.u = c->u.p;
-    a.dd = c->dd.p;
+    a.sc = ln.sc.p;
+    a.dg = ln.dg.p;
+    a.u = ln.u.p;
+    a.dd = ln.dd.p;
     return a;
 }
 
 // Steps a1-a5 for one wave whose plan inputs (counts[0], cluster, src_ct,
 // src_key, dst_out of wp) are already on the device, in stream order.
-int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t st)
+int run_wave(wally_ctx *c, Lane &ln, const WavePlan &wp, uint32_t wave_len, cudaStream_t st)
 {
     const DevParams &dp = c->dp;
     const size_t ctw = c->ctw(), keysw = c->keysw();
     const uint32_t L = c->L, g = c->g, h = c->h;
     CUDA_TRY(launch_wave_plan(wp, c->d_chunks.p, wave_len, st, c->pr()));
     // a1: ciphertexts into slot 0 of the baby-step array, keys (Montgomery)
-    CUDA_TRY(launch_to_ntt(dp, wp.src_ct, nullptr, 0, c->ctp.p, (size_t)g * ctw, 2 * L, L, wave_len, wp.counts,
+    CUDA_TRY(launch_to_ntt(dp, wp.src_ct, nullptr, 0, ln.ctp.p, (size_t)g * ctw, 2 * L, L, wave_len, wp.counts,
                            false, st, c->pr()));
-    CUDA_TRY(launch_to_ntt(dp, wp.src_key, nullptr, 0, c->keysN.p, keysw, 4 * L * (L + 1), L + 1, wave_len,
+    CUDA_TRY(launch_to_ntt(dp, wp.src_key, nullptr, 0, ln.keysN.p, keysw, 4 * L * (L + 1), L + 1, wave_len,
                            wp.counts, true, st, c->pr()));
     // a2: ct'[j] = Rot_1(ct'[j-1])
     for (uint32_t j = 1; j < g; j++) {
-        RotArgs a = rot_args(c);
-        a.src = c->ctp.p + (size_t)(j - 1) * ctw;
+        RotArgs a = rot_args(ln);
+        a.src = ln.ctp.p + (size_t)(j - 1) * ctw;
         a.src_stride = (size_t)g * ctw;
-        a.dst = c->ctp.p + (size_t)j * ctw;
+        a.dst = ln.ctp.p + (size_t)j * ctw;
         a.dst_stride = (size_t)g * ctw;
-        a.key = c->keysN.p;
+        a.key = ln.keysN.p;
         a.key_stride = keysw;
         a.n_max = wave_len;
         a.n_dev = wp.counts;
@@ -359,23 +384,23 @@ int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t s
         CUDA_TRY(launch_rotate(dp, a, st, c->pr()));
     }
     // a3: T_i = sum_b P'_{k,i,b} ct'[b]
-    CUDA_TRY(launch_mac(dp, cluster_store(c), wp, c->ctp.p, c->T.p, wave_len, c->m_max, c->num_sms, st, c->pr()));
+    CUDA_TRY(launch_mac(dp, cluster_store(c), wp, ln.ctp.p, ln.T.p, wave_len, c->m_max, c->num_sms, st, c->pr()));
     // a4: S = T_{h-1}; S = Rot_g(S) + T_i, i = h-2 .. 0
     const uint32_t np_max = wave_len * c->m_max;
     for (int i = (int)h - 2; i >= 0; i--) {
-        RotArgs a = rot_args(c);
+        RotArgs a = rot_args(ln);
         if (i == (int)h - 2) {
-            a.src = c->T.p + (size_t)(h - 1) * ctw;
+            a.src = ln.T.p + (size_t)(h - 1) * ctw;
             a.src_stride = (size_t)h * ctw;
         } else {
-            a.src = c->S.p;
+            a.src = ln.S.p;
             a.src_stride = ctw;
         }
-        a.dst = c->S.p;
+        a.dst = ln.S.p;
         a.dst_stride = ctw;
-        a.add = c->T.p + (size_t)i * ctw;
+        a.add = ln.T.p + (size_t)i * ctw;
         a.add_stride = (size_t)h * ctw;
-        a.key = c->keysN.p + keysw / 2;
+        a.key = ln.keysN.p + keysw / 2;
         a.key_stride = keysw;
         a.key_map = wp.pair_pos;
         a.n_max = np_max;
@@ -386,8 +411,8 @@ int run_wave(wally_ctx *c, const WavePlan &wp, uint32_t wave_len, cudaStream_t s
         CUDA_TRY(launch_rotate(dp, a, st, c->pr()));
     }
     // a5: back to coefficient form, into the caller's output
-    if (h == 1) CUDA_TRY(launch_output(dp, wp, c->T.p, ctw, np_max, st, c->pr()));
-    else CUDA_TRY(launch_output(dp, wp, c->S.p, ctw, np_max, st, c->pr()));
+    if (h == 1) CUDA_TRY(launch_output(dp, wp, ln.T.p, ctw, np_max, st, c->pr()));
+    else CUDA_TRY(launch_output(dp, wp, ln.S.p, ctw, np_max, st, c->pr()));
     return WALLY_OK;
 }
 
@@ -497,20 +522,7 @@ void wally_destroy(wally_ctx *c)
     c->ptxt.release();
     c->d_chunks.release();
     c->d_chunk0.release();
-    c->keysN.release();
-    c->ctp.release();
-    c->T.release();
-    c->S.release();
-    c->sc.release();
-    c->dg.release();
-    c->u.release();
-    c->dd.release();
-    c->plan_u32.release();
-    c->plan_ptr.release();
-    c->counts.release();
-    c->cstart.release();
-    c->fill.release();
-    c->sorted_q.release();
+    for (Lane &ln : c->lanes) ln.release();
     for (int b = 0; b < 2; b++) {
         c->stage_ct[b].release();
         c->stage_key[b].release();
@@ -645,33 +657,42 @@ int wally_export_cluster(wally_ctx *c, uint32_t id, uint64_t *out, void *stream)
     return WALLY_OK;
 }
 
-int wally_eval_batch(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
-                     const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out, void *stream)
+int wally_eval_batch_lane(wally_ctx *c, uint32_t lane, uint32_t n, const uint32_t *ids, const uint64_t *cts,
+                          const uint64_t *keys, const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out,
+                          void *stream)
 {
     if (!c) return fail(WALLY_EINVAL, "null context");
     if (!c->num_clusters) return fail(WALLY_ESTATE, "no clusters loaded");
     if (n == 0) return WALLY_OK;
     if (!ids || !cts || !keys || !out_offsets || !out) return fail(WALLY_EINVAL, "null argument");
     if (!aligned16(cts) || !aligned16(keys) || !aligned16(out)) return fail(WALLY_EINVAL, "buffers must be 16-byte aligned");
+    if (lane >= WALLY_MAX_LANES) return fail(WALLY_EINVAL, "lane %u out of range (%d lanes)", lane, WALLY_MAX_LANES);
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t W = c->max_wave;
-    int rc = ensure_workspace(c, W, c->m_max);
+    Lane &ln = c->lanes[lane];
+    int rc = ensure_workspace(c, ln, W, c->m_max);
     if (rc) return rc;
     const uint32_t K = c->num_clusters;
-    if (c->counts.ensure(K) != cudaSuccess || c->cstart.ensure(K + 1) != cudaSuccess ||
-        c->fill.ensure(K) != cudaSuccess || c->sorted_q.ensure(n) != cudaSuccess)
+    if (ln.counts.ensure(K) != cudaSuccess || ln.cstart.ensure(K + 1) != cudaSuccess ||
+        ln.fill.ensure(K) != cudaSuccess || ln.sorted_q.ensure(n) != cudaSuccess)
         return fail(WALLY_ENOMEM, "cannot allocate the grouping arrays");
     // a0: group by cluster
-    CUDA_TRY(launch_group(ids, n, K, c->counts.p, c->cstart.p, c->fill.p, c->sorted_q.p, c->d_err, st));
+    CUDA_TRY(launch_group(ids, n, K, ln.counts.p, ln.cstart.p, ln.fill.p, ln.sorted_q.p, c->d_err, st));
     for (uint32_t wb = 0; wb < n; wb += W) {
         const uint32_t len = std::min(W, n - wb);
-        CUDA_TRY(launch_gather_wave(c->wp, c->sorted_q.p, ids, c->cstart.p, K, wb, len, cts, keys, input_index,
+        CUDA_TRY(launch_gather_wave(ln.wp, ln.sorted_q.p, ids, ln.cstart.p, K, wb, len, cts, keys, input_index,
                                     out_offsets, out, c->ctw(), c->keysw(), st));
-        rc = run_wave(c, c->wp, len, st);
+        rc = run_wave(c, ln, ln.wp, len, st);
         if (rc) return rc;
     }
     return WALLY_OK;
+}
+
+int wally_eval_batch(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
+                     const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out, void *stream)
+{
+    return wally_eval_batch_lane(c, 0, n, ids, cts, keys, input_index, out_offsets, out, stream);
 }
 
 int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
@@ -686,7 +707,8 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
     const uint32_t K = c->num_clusters, W = c->max_wave;
     for (uint32_t q = 0; q < n; q++)
         if (ids[q] >= K) return fail(WALLY_EINVAL, "query %u names cluster %u of %u", q, ids[q], K);
-    int rc = ensure_workspace(c, W, c->m_max);
+    Lane &ln = c->lanes[0];
+    int rc = ensure_workspace(c, ln, W, c->m_max);
     if (rc) return rc;
     const size_t ctw = c->ctw(), keysw = c->keysw();
     for (int b = 0; b < 2; b++) {
@@ -752,7 +774,7 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
             }
         }
         if (rc) break;
-        WavePlan wp = c->wp;
+        WavePlan wp = ln.wp;
         wp.counts = c->stage_cluster[b].p;
         wp.cluster = c->stage_cluster[b].p + 4;
         wp.src_ct = (const u64 **)c->stage_ptrs[b].p;
@@ -763,7 +785,7 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
         CUDA_TRY(cudaEventRecord(in_done[b], cin));
         CUDA_TRY(cudaStreamWaitEvent(st, in_done[b], 0));
         CUDA_TRY(cudaStreamWaitEvent(st, out_done[b], 0));
-        rc = run_wave(c, wp, len, st);
+        rc = run_wave(c, ln, wp, len, st);
         if (rc) break;
         CUDA_TRY(cudaEventRecord(comp_done[b], st));
         CUDA_TRY(cudaStreamWaitEvent(cout_, comp_done[b], 0));
@@ -802,27 +824,28 @@ int wally_rotate(wally_ctx *c, uint32_t n, uint64_t k, const uint64_t *cts, cons
     if ((k & 1) == 0 || k >= 2 * (uint64_t)c->N) return fail(WALLY_EINVAL, "Galois element must be odd and < 2N");
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = ensure_workspace(c, c->max_wave, std::max<uint32_t>(c->m_max, 1));
+    Lane &ln = c->lanes[0];
+    int rc = ensure_workspace(c, ln, c->max_wave, std::max<uint32_t>(c->m_max, 1));
     if (rc) return rc;
     const size_t ctw = c->ctw(), keyw = c->keysw() / 2;
     const uint32_t chunk = c->max_wave;
     for (uint32_t x0 = 0; x0 < n; x0 += chunk) {
         const uint32_t cnt = std::min(chunk, n - x0);
-        CUDA_TRY(launch_to_ntt(c->dp, nullptr, cts + (size_t)x0 * ctw, ctw, c->S.p, ctw, 2 * c->L, c->L, cnt, nullptr,
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, cts + (size_t)x0 * ctw, ctw, ln.S.p, ctw, 2 * c->L, c->L, cnt, nullptr,
                                false, st));
-        CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)x0 * keyw, keyw, c->keysN.p, keyw,
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)x0 * keyw, keyw, ln.keysN.p, keyw,
                                2 * c->L * (c->L + 1), c->L + 1, cnt, nullptr, true, st));
-        RotArgs a = rot_args(c);
-        a.src = c->S.p;
+        RotArgs a = rot_args(ln);
+        a.src = ln.S.p;
         a.src_stride = ctw;
-        a.dst = c->S.p;
+        a.dst = ln.S.p;
         a.dst_stride = ctw;
-        a.key = c->keysN.p;
+        a.key = ln.keysN.p;
         a.key_stride = keyw;
         a.n_max = cnt;
         a.galois = k;
         CUDA_TRY(launch_rotate(c->dp, a, st));
-        CUDA_TRY(launch_from_ntt(c->dp, c->S.p, out + (size_t)x0 * ctw, 2 * c->L, c->L, cnt, st));
+        CUDA_TRY(launch_from_ntt(c->dp, ln.S.p, out + (size_t)x0 * ctw, 2 * c->L, c->L, cnt, st));
     }
     return WALLY_OK;
 }

@@ -63,6 +63,7 @@ SIGNATURES = {
     "wally_cluster_chunks": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(_u32)]),
     "wally_export_cluster": (ctypes.c_int, [_vp, _u32, _vp, _vp]),
     "wally_eval_batch": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "wally_eval_batch_lane": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "wally_eval_batch_host": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "wally_rotate": (ctypes.c_int, [_vp, _u32, _u64, _vp, _vp, _vp, _vp]),
     "wally_rotate_noalloc": (ctypes.c_int, [_vp, _u32, _u64, _vp, _vp, _vp, _vp]),
@@ -182,6 +183,13 @@ def wally_eval_batch(ctx: int, n: int, cluster_ids, cts, galois_keys, input_inde
     _require_cuda(cluster_ids, cts, galois_keys, input_index, out_offsets, out)
     _check(load().wally_eval_batch(ctx, n, _ptr(cluster_ids), _ptr(cts), _ptr(galois_keys), _ptr(input_index),
                                    _ptr(out_offsets), _ptr(out), _stream(stream)))
+
+
+def wally_eval_batch_lane(ctx: int, lane: int, n: int, cluster_ids, cts, galois_keys, input_index, out_offsets,
+                          out, stream=None) -> None:
+    _require_cuda(cluster_ids, cts, galois_keys, input_index, out_offsets, out)
+    _check(load().wally_eval_batch_lane(ctx, lane, n, _ptr(cluster_ids), _ptr(cts), _ptr(galois_keys),
+                                        _ptr(input_index), _ptr(out_offsets), _ptr(out), _stream(stream)))
 
 
 def wally_eval_batch_host(ctx: int, n: int, cluster_ids, cts, galois_keys, input_index, out_offsets, out,

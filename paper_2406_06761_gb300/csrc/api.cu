@@ -221,6 +221,8 @@ int setup_tables(wally_ctx *c)
         Mod &md = dp.m[j];
         md.p = p;
         md.two_p = 2 * p;
+        md.four_p = 4 * p;
+        md.np = (uint64_t)0 - p;
         md.mont_neg_inv = mont_neg_inv(p);
         const uint64_t r = (uint64_t)(((u128)1 << 64) % p);
         md.r2 = mulmod_h(r, r, p);

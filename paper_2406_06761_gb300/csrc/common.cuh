@@ -12,8 +12,10 @@
 //    sums of up to 2^12 products of residues < p (Sec. 7 "lazy reduction" in
 //    sequential plaintext-ciphertext products) stay below that bound.
 //  - Harvey's lazy butterflies (Harvey 2014, the NTT the paper's library uses,
-//    Sec. 7): forward Cooley-Tukey values in [0, 4p), inverse Gentleman-Sande
-//    values in [0, 2p).
+//    Sec. 7), with a Shoup quotient taken from the three high 32x32 partial
+//    products only (short by at most 2, so the product lies in [0, 4p)):
+//    forward Cooley-Tukey values in [0, 8p), inverse Gentleman-Sande values in
+//    [0, 4p).  With p < 2^50 every value stays below 2^53.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -34,7 +36,8 @@ struct __align__(16) Tw {
 // One RNS modulus with its NTT tables (device pointers, N entries each):
 // fwd[k] = psi^brv(k), inv[k] = psi^-brv(k), brv = bit reversal on log2 N bits.
 struct Mod {
-    u64 p, two_p;
+    u64 p, two_p, four_p;
+    u64 np;            // 2^64 - p
     u64 mont_neg_inv;  // -p^-1 mod 2^64
     u64 r2;            // 2^128 mod p
     u64 n_inv, n_inv_s;
@@ -131,19 +134,32 @@ __host__ __device__ constexpr int ntt_smem_words()
     return smem_words(1 << LOGN) + 2 * NttShape<LOGN>::TW_CACHE;
 }
 
-__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 p, u64 two_p)
+// x * w mod p up to 3p: a value in [0, 4p) for any x < 2^64.  The quotient
+// x * w' / 2^64 is built from x1*s1, hi(x1*s0) and hi(x0*s1) (x = x1:x0,
+// w' = s1:s0 in 32-bit halves); the dropped terms add less than 3 * 2^32 to
+// the middle column, so it is short by at most 2.  np = 2^64 - p.
+__device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 ws, u64 np)
 {
-    u64 x = csub(X, two_p);
-    u64 t = shoup_mul(Y, w, ws, p);
-    X = x + t;
-    Y = x - t + two_p;
+    const u32 x0 = (u32)x, x1 = (u32)(x >> 32), s0 = (u32)ws, s1 = (u32)(ws >> 32);
+    const u64 q = (u64)x1 * s1 + __umulhi(x1, s0) + __umulhi(x0, s1);
+    return x * w + q * np;
 }
 
-__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 p, u64 two_p)
+// Forward butterfly, values in [0, 8p).
+__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 np, u64 four_p)
+{
+    u64 x = csub(X, four_p);
+    u64 t = shoup_lazy(Y, w, ws, np);
+    X = x + t;
+    Y = x - t + four_p;
+}
+
+// Inverse butterfly, values in [0, 4p).
+__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 np, u64 four_p)
 {
     u64 x = X, y = Y;
-    X = csub(x + y, two_p);
-    Y = shoup_mul(x - y + two_p, w, ws, p);
+    X = csub(x + y, four_p);
+    Y = shoup_lazy(x - y + four_p, w, ws, np);
 }
 
 // Copy table entries [0, TW_CACHE) into the shared cache.
@@ -225,14 +241,14 @@ __device__ __forceinline__ void ntt_pass(u64 *sm, int S0, const Tw *tws, u64 p, 
 }
 
 // Forward negacyclic NTT in place: natural-order coefficients (any values
-// < 4p) -> evaluations at psi^(2*brv(i)+1) in bit-reversed position i, values
-// in [0, 4p).  cache: TW_CACHE shared entries (reloaded here).  Starts and
+// < 8p) -> evaluations at psi^(2*brv(i)+1) in bit-reversed position i, values
+// in [0, 8p).  cache: TW_CACHE shared entries (reloaded here).  Starts and
 // ends with __syncthreads().
 template <int LOGN>
 __device__ __forceinline__ void ntt_fwd(u64 *sm, Tw *cache, const Mod &md)
 {
     using S = NttShape<LOGN>;
-    const u64 p = md.p, two_p = md.two_p;
+    const u64 p = md.np, two_p = md.four_p;  // the butterflies take (2^64 - p, 4p)
     __syncthreads();
     load_tw_cache<LOGN>(cache, md.fwd);
     __syncthreads();
@@ -249,14 +265,14 @@ __device__ __forceinline__ void ntt_fwd(u64 *sm, Tw *cache, const Mod &md)
     __syncthreads();
 }
 
-// Inverse: bit-reversed evaluations (values < 2p) -> natural-order
-// coefficients times N (values in [0, 2p)); callers scale by N^-1 with
+// Inverse: bit-reversed evaluations (values < 4p) -> natural-order
+// coefficients times N (values in [0, 4p)); callers scale by N^-1 with
 // inv_finish().  Starts and ends with __syncthreads().
 template <int LOGN>
 __device__ __forceinline__ void ntt_inv(u64 *sm, Tw *cache, const Mod &md)
 {
     using S = NttShape<LOGN>;
-    const u64 p = md.p, two_p = md.two_p;
+    const u64 p = md.np, two_p = md.four_p;  // the butterflies take (2^64 - p, 4p)
     __syncthreads();
     load_tw_cache<LOGN>(cache, md.inv);
     ntt_pass<LOGN, 4, false>(sm, LOGN - 4, md.inv, p, two_p);
@@ -272,8 +288,8 @@ __device__ __forceinline__ void ntt_inv(u64 *sm, Tw *cache, const Mod &md)
     }
 }
 
-// [0, 4p) -> [0, p)
-__device__ __forceinline__ u64 fwd_finish(u64 x, const Mod &md) { return csub(csub(x, md.two_p), md.p); }
+// [0, 8p) -> [0, p)
+__device__ __forceinline__ u64 fwd_finish(u64 x, const Mod &md) { return csub(csub(csub(x, md.four_p), md.two_p), md.p); }
 // N^-1 scaling after ntt_inv, canonical result.
 __device__ __forceinline__ u64 inv_finish(u64 x, const Mod &md) { return csub(shoup_mul(x, md.n_inv, md.n_inv_s, md.p), md.p); }
 
@@ -303,6 +319,14 @@ __device__ __forceinline__ int pair_elem(int u)
 __device__ __forceinline__ ulonglong2 ldg2(const u64 *p) { return __ldg(reinterpret_cast<const ulonglong2 *>(p)); }
 __device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
 __device__ __forceinline__ void st2(u64 *p, u64 a, u64 b) { *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(a, b); }
+
+// Bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2 by the
+// copy engine of the SM (TMA), without waiting: the data a CTA needs only
+// after its transforms is requested at its start.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // Global polynomial -> shared buffer (any values), 16-byte loads.  COHERENT:
 // the data was written earlier by this kernel (read through the coherent

@@ -48,7 +48,7 @@ struct Smem {
 
 // ---------------------------------------------------------------- a1: to NTT form
 // Item x, polynomial z (modulus z % mod_cycle): forward NTT of the input
-// (coefficients < 4p), canonical output, optionally times 2^64 (Montgomery).
+// (coefficients < 8p), canonical output, optionally times 2^64 (Montgomery).
 template <int LOGN>
 __global__ void NTT_LB(LOGN) k_to_ntt(const DevParams *dpp, const u64 *const *src_ptrs, const u64 *src,
                                       size_t src_stride, u64 *dst, size_t dst_stride, u32 mod_cycle, u32 n_max,
@@ -166,14 +166,14 @@ __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
     for (int i = 0; i < L; i++) {
         if (i == j) continue;
         __syncthreads();
-        poly_load<LOGN>(S.poly, a.dg + ((size_t)x * L + i) * N);  // < q_i < 4 p_j
+        poly_load<LOGN>(S.poly, a.dg + ((size_t)x * L + i) * N);  // < q_i < 8 p_j
         ntt_fwd<LOGN>(S.poly, S.twf, md);
         if (i != last) {
             u64 *di = dd + (size_t)i * N;
 #pragma unroll 4
             for (int u = 0; u < 16; u++) {
                 const int e = pair_elem<LOGN>(u), sp = spos(e);
-                st2(di + e, S.poly[sp], S.poly[sp ^ 1]);  // lazy, < 4 p_j
+                st2(di + e, S.poly[sp], S.poly[sp ^ 1]);  // lazy, < 8 p_j
             }
         }
     }

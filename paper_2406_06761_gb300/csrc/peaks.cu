@@ -37,10 +37,10 @@ __global__ void __launch_bounds__(256) k_peak_bfly(u64 w, u64 ws, u64 *sink)
         x[c] = threadIdx.x * 7919ull + c * 104729ull + blockIdx.x;
         y[c] = x[c] ^ 0x5555ull;
     }
-    const u64 two_p = 2 * PRIME;
+    const u64 four_p = 4 * PRIME, np = (u64)0 - PRIME;
     for (int it = 0; it < ITERS; it++) {
 #pragma unroll
-        for (int c = 0; c < CHAINS; c++) ct_bfly(x[c], y[c], w, ws, PRIME, two_p);
+        for (int c = 0; c < CHAINS; c++) ct_bfly(x[c], y[c], w, ws, np, four_p);
     }
     u64 acc = 0;
 #pragma unroll

@@ -10,6 +10,7 @@ import torch
 import oracle as O
 from paper_2406_06761_gb300 import harness as H
 from paper_2406_06761_gb300 import wally as Wl
+from paper_2406_06761_gb300 import workload as W
 
 pytestmark = pytest.mark.gpu
 
@@ -78,4 +79,100 @@ def test_batched_workload_full_size():
     for qi in sorted(picks):
         m = int(wl.chunks[wl.ids[qi]])
         _oracle_check(wl, prm, qi, got[offs[qi]:offs[qi] + m])
+    wl.close()
+
+
+def test_wide_workload_sampled():
+    """Wide embeddings: N = 16384, six 50-bit limbs, d = 768 (g = h = 32),
+    entries in [-7, 7]; two clusters, a real and a fake query, bit for bit."""
+    w = W.WORKLOADS["wide"]
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    ctx = Wl.Context(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim, max_wave=2)
+    sizes = np.array([1000, 37], np.uint32)
+    E = W.embeddings(int(sizes.sum()), w.dim, w.entry_bound, seed=51)
+    Wl.wally_load_clusters(ctx.ptr, sizes, E)
+    cr = W.client_randomness(2, prm.N, prm.q, prm.P, seed=51)
+    q = W.query_vectors(1, w.dim, w.entry_bound, seed=51)[0]
+    keys = np.stack([O.keygen_pair(prm, cr.secret[i], cr.key_a[i], cr.key_e[i]) for i in range(2)])
+    cts = np.stack([O.encrypt_query(prm, cr.secret[0], q, cr.enc_a[0], cr.enc_e[0]),
+                    O.encrypt_query(prm, cr.secret[1], None, cr.enc_a[1], cr.enc_e[1])])
+    dev = torch.device("cuda", 0)
+    out = torch.empty((2, 2, prm.L, prm.N), dtype=torch.int64, device=dev)
+    Wl.wally_eval_batch(ctx.ptr, 2, torch.tensor([0, 1], dtype=torch.int32, device=dev), Wl.u64_tensor(cts, dev),
+                        Wl.u64_tensor(keys, dev), None, torch.tensor([0, 1], dtype=torch.int64, device=dev), out)
+    Wl.wally_sync(ctx.ptr)
+    got = Wl.to_u64_numpy(out)
+    m, pt = O.encode_cluster(prm, E[:1000])
+    assert np.array_equal(got[0], O.eval_query(prm, m, pt, cts[0], keys[0])[0])
+    scores = torch.empty((2, prm.N), dtype=torch.int64, device=dev)
+    Wl.wally_decrypt_scores(ctx.ptr, 2, torch.from_numpy(cr.secret).to(dev), None, out, scores)
+    sc = scores.cpu().numpy()
+    assert np.array_equal(sc[0, :1000], E[:1000].astype(np.int64) @ q.astype(np.int64))
+    assert np.all(sc[0, 1000:] == 0) and np.all(sc[1] == 0)
+    ctx.close()
+
+
+def test_full_scale_batch_sampled():
+    """The full-scale batch as bench.py runs it: 3.2M x 192 in 1,800 clusters,
+    500,000 real queries + fakes, a 2,048-client pool, waves of 1,024, the
+    batch split into calls whose outputs share one buffer.  Sampled outputs
+    are checked bit for bit against the oracle, and a larger sample by GPU
+    decryption against the plain dot products."""
+    wl = H.DeviceWorkload("full_scale", pool=2048, max_wave=1024)
+    prm = O.params(wl.w.log_n, wl.w.num_q, wl.w.q_bits, wl.w.t_bits, wl.w.dim)
+    free, _ = torch.cuda.mem_get_info(wl.dev)
+    subs = wl.sub_batches(int(free * 0.5))
+    rng = np.random.default_rng(7)
+    exact = set(rng.choice(wl.n, size=4, replace=False).tolist()) | {0, wl.n - 1}
+    exact.add(int(np.flatnonzero(~wl.is_real)[0]))
+    decrypt = set(rng.choice(wl.n, size=256, replace=False).tolist())
+    keep = {}
+    out = None
+    for lo, hi in subs:
+        b = wl.device_batch(lo, hi)
+        if out is None or out.shape[0] < b[3]:
+            out = wl.alloc_out(max(b[3], 1))
+        wl.eval(b, out[:b[3]])
+        Wl.wally_sync(wl.ctx.ptr)
+        offs = b[4]
+        for qi in (exact | decrypt):
+            if lo <= qi < hi:
+                m = int(wl.chunks[wl.ids[qi]])
+                keep[qi] = out[int(offs[qi - lo]):int(offs[qi - lo]) + m].clone()
+    assert len(subs) >= 1 and len(keep) == len(exact | decrypt)
+    secrets = wl.secrets()
+    for qi in sorted(decrypt | exact):
+        ct = keep[qi]
+        e = int(wl.input_index[qi])
+        scores = torch.empty((ct.shape[0], wl.N), dtype=torch.int64, device=wl.dev)
+        Wl.wally_decrypt_scores(wl.ctx.ptr, ct.shape[0], torch.from_numpy(secrets[e:e + 1]).to(wl.dev),
+                                torch.zeros(ct.shape[0], dtype=torch.int32, device=wl.dev), ct.contiguous(), scores)
+        sc = scores.cpu().numpy().reshape(-1)
+        expect = wl.expected_scores(int(wl.ids[qi]), wl.entry_query(e))
+        assert np.array_equal(sc[:len(expect)], expect) and np.all(sc[len(expect):] == 0), qi
+    for qi in sorted(exact):
+        _oracle_check(wl, prm, qi, Wl.to_u64_numpy(keep[qi]))
+    wl.close()
+
+
+def test_eval_batch_captured_in_a_cuda_graph():
+    """The whole batched evaluation (grouping, waves, every kernel) captured
+    once in a CUDA graph and replayed gives the same outputs."""
+    wl = H.DeviceWorkload("batched", max_wave=512)
+    ids, idx, offs_d, chunks, offs = wl.device_batch(0, wl.n)
+    ref = wl.alloc_out(chunks)
+    wl.eval((ids, idx, offs_d, chunks, offs), ref)
+    Wl.wally_sync(wl.ctx.ptr)
+    out = wl.alloc_out(chunks)
+    out.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        wl.eval((ids, idx, offs_d, chunks, offs), out)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    Wl.wally_sync(wl.ctx.ptr)
     wl.close()

@@ -82,6 +82,8 @@ def _load():
                 "or_ptct_sum": (None, [_pp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
                 "or_ptxt_to_ntt": (None, [_pp, ctypes.c_uint32, _u64p, _u64p]),
                 "or_eval": (ctypes.c_int, [_pp, ctypes.c_uint32, _u64p, _u64p, _u64p, _u64p]),
+                "or_compress": (None, [_pp, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u64p]),
+                "or_decompress_residue": (None, [_pp, _i8p, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u64p]),
                 "or_eval_batch": (ctypes.c_int, [_pp, ctypes.c_uint32, _u32p, ctypes.POINTER(_u64p), ctypes.c_uint32,
                                                  _u32p, _u64p, _u64p, _u64p, _u64p, ctypes.c_uint32]),
             }
@@ -386,3 +388,35 @@ def eval_batch(prm: Params, clusters_ntt: list, ids, cts, keys, nthreads: int | 
     if rc != 0:
         raise ValueError("or_eval_batch rejected the input")
     return out, offs.astype(np.int64)
+
+
+# ------------------------------------------------------------------ response compression
+
+def drop_bits(q_last: int, t: int, n: int, z: float = 8.0) -> tuple[int, int]:
+    """Bits dropped from c0 and c1 (Sec. 7 "Reducing the response size"):
+    l0 = floor(log2(q'/t) - 2), l1 = floor(log2(q'/t) - 2 - log2(z sqrt(2n/9)))."""
+    import math
+    r = math.log2(q_last / t)
+    l0 = max(0, math.floor(r - 2))
+    l1 = max(0, math.floor(r - 2 - math.log2(z * math.sqrt(2 * n / 9))))
+    return l0, l1
+
+
+def compress(prm: Params, ct, l0: int, l1: int) -> np.ndarray:
+    """Switch a response to its last limb and drop l0 / l1 low bits: [2][N]."""
+    ct = _u64(ct)
+    out = np.empty((2, prm.N), np.uint64)
+    _load().or_compress(prm.ptr, _p(ct, _u64p), l0, l1, _p(out, _u64p))
+    return out
+
+
+def decrypt_compressed_slots(prm: Params, s, cc, l0: int, l1: int) -> np.ndarray:
+    """m = round(t x / q') mod t with x = c0'' 2^l0 + c1'' 2^l1 s (mod q'),
+    decoded to slots and centred."""
+    s, cc = _i8(s), _u64(cc)
+    x = np.empty(prm.N, np.uint64)
+    _load().or_decompress_residue(prm.ptr, _p(s, _i8p), _p(cc, _u64p), l0, l1, _p(x, _u64p))
+    q, t = prm.q[-1], prm.t
+    m = np.array([((t * int(v) + q // 2) // q) % t for v in x], dtype=np.uint64)
+    v = slots_decode(prm, m).astype(np.int64)
+    return np.where(v > t // 2, v - t, v)

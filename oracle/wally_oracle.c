@@ -30,6 +30,9 @@
  *      smallest x with x^N = -1 (mod t)
  *   R8 d is padded to the next power of two; g = 2^ceil(log2(d_pad)/2)
  *   R9 plaintext polynomials are lifted centred before reduction mod q_i
+ *   R16 the response switch to the last limb is a chain of exact rescalings
+ *      by q_0, ..., q_{L-2}, each rounding to nearest; dropped bits round to
+ *      nearest too
  *
  * Parity status: every function here is pinned by a test against something
  * other than itself (closed forms, Python big-integer re-derivations,
@@ -675,4 +678,54 @@ int or_eval_batch(const or_params *o, uint32_t n_clusters, const uint32_t *chunk
     for (uint32_t i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
     free(th);
     return 0;
+}
+
+/* ---------------------------------------------------------------- response compression
+ * Sec. 7 "Reducing the response size": switch the response to its last RNS
+ * limb q' = q_{L-1} and drop low bits of both polynomials.
+ * Reading R16: the switch is a chain of exact rescalings by q_0, ..., q_{L-2};
+ * each step replaces c by round(c / q_i), computed as
+ * (c - [c]_{q_i, centred}) * q_i^-1 on the remaining limbs.  Then l0 low bits
+ * of c0 and l1 of c1 are dropped with rounding to nearest:
+ * c'' = floor((c' + 2^(l-1)) / 2^l).  Output [2][N] integers. */
+void or_compress(const or_params *o, const uint64_t *ct, uint32_t l0, uint32_t l1, uint64_t *out)
+{
+    uint32_t N = o->N, L = o->L;
+    int64_t v[OR_MAX_MODS];
+    for (uint32_t c = 0; c < 2; c++)
+        for (uint32_t n = 0; n < N; n++) {
+            for (uint32_t j = 0; j < L; j++) v[j] = (int64_t)ct[((size_t)c * L + j) * N + n];
+            for (uint32_t i = 0; i + 1 < L; i++) {
+                uint64_t qi = o->mod[i];
+                int64_t rc = (uint64_t)v[i] > (qi - 1) / 2 ? v[i] - (int64_t)qi : v[i];
+                for (uint32_t j = i + 1; j < L; j++) {
+                    uint64_t qj = o->mod[j];
+                    uint64_t d = submod((uint64_t)v[j], smod(rc, qj), qj);
+                    v[j] = (int64_t)mulmod(d, invmod(qi % qj, qj), qj);
+                }
+            }
+            uint64_t x = (uint64_t)v[L - 1];
+            uint32_t l = c ? l1 : l0;
+            out[(size_t)c * N + n] = l ? (x + ((uint64_t)1 << (l - 1))) >> l : x;
+        }
+}
+
+/* Decryption of a compressed response, first half: x = c0'' 2^l0 +
+ * c1'' 2^l1 s (mod q'); the scaling round(t x / q') is left to the caller. */
+void or_decompress_residue(const or_params *o, const int8_t *s, const uint64_t *cc, uint32_t l0, uint32_t l1,
+                           uint64_t *x)
+{
+    uint32_t N = o->N, L = o->L;
+    uint64_t q = o->mod[L - 1];
+    uint64_t *c1 = (uint64_t *)malloc(8 * (size_t)N), *sj = (uint64_t *)malloc(8 * (size_t)N);
+    uint64_t *p = (uint64_t *)malloc(8 * (size_t)N);
+    for (uint32_t n = 0; n < N; n++) {
+        c1[n] = mulmod(cc[N + n] % q, powmod(2, l1, q), q);
+        sj[n] = smod(s[n], q);
+    }
+    or_polymul(o, L - 1, c1, sj, p);
+    for (uint32_t n = 0; n < N; n++) x[n] = addmod(mulmod(cc[n] % q, powmod(2, l0, q), q), p[n], q);
+    free(c1);
+    free(sj);
+    free(p);
 }

@@ -409,3 +409,52 @@ def test_eval_batch_equals_single(tiny_params):
     for i, c in enumerate(ids):
         m, pt = (m1, p1) if c == 0 else (m2, p2)
         assert np.array_equal(out[offs[i]:offs[i] + m], O.eval_query(prm, m, pt, cts[i], keys[i]))
+
+
+# ------------------------------------------------------------------ response compression
+
+def test_drop_bits_worked_example():
+    """Sec. 7: n = 4096, 27-bit last limb, 16-bit t, z = 8 -> l0 = 9, l1 <= 1
+    (the paper uses 0); 55 KB -> 23.5 KB (tests/golden/response_size_sec7.txt)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "response_size_sec7.txt")) if l.strip() and l[0] != "#"]
+    for n, qb, tb, z, l0_paper, l1_used, kb in rows:
+        n, qb, tb, l0_paper, l1_used = int(n), int(qb), int(tb), int(l0_paper), int(l1_used)
+        l0, l1_max = O.drop_bits(2 ** qb, 2 ** tb, n, float(z))
+        assert l0 == l0_paper and 0 <= l1_used <= l1_max
+        size_kb = n * ((qb - l0) + (qb - l1_used)) / 8 / 1000
+        assert abs(size_kb - float(kb)) / float(kb) < 0.03
+
+
+def test_compress_is_a_chain_of_rounded_divisions(small_params):
+    """Reading R16 against big integers: c' = round(...round(c / q_0)... / q_{L-2})
+    mod q_{L-1}, then floor((c' + 2^(l-1)) / 2^l)."""
+    for prm in (small_params, O.params(4, 3, 30, 10, 4)):
+        rng = _rng(40)
+        ct = np.stack([np.stack([rng.integers(0, q, size=prm.N, dtype=np.uint64) for q in prm.q]) for _ in range(2)])
+        l0, l1 = 7, 3
+        got = O.compress(prm, ct, l0, l1)
+        for c, l in ((0, l0), (1, l1)):
+            comp = B.poly_crt(ct[c], prm.q)
+            for n in range(prm.N):
+                v, mod = comp[n], prm.Q
+                for qi in prm.q[:-1]:
+                    v = (2 * v + qi) // (2 * qi)   # nearest integer to v / q_i (q_i odd)
+                    mod //= qi
+                    v %= mod
+                assert int(got[c][n]) == (v + (1 << (l - 1))) >> l
+
+
+def test_compressed_tiny_response_decrypts(tiny_params):
+    prm = tiny_params
+    w = W.WORKLOADS["tiny"]
+    E = W.embeddings(1024, w.dim, w.entry_bound)
+    q = W.query_vectors(1, w.dim, w.entry_bound)[0]
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P)
+    m, pt = O.encode_cluster(prm, E)
+    keys = O.keygen_pair(prm, cr.secret[0], cr.key_a[0], cr.key_e[0])
+    ct = O.encrypt_query(prm, cr.secret[0], q, cr.enc_a[0], cr.enc_e[0])
+    out = O.eval_query(prm, m, pt, ct, keys)[0]
+    l0, l1 = O.drop_bits(prm.q[-1], prm.t, prm.N)
+    cc = O.compress(prm, out, l0, l1)
+    sc = O.decrypt_compressed_slots(prm, cr.secret[0], cc, l0, l1)
+    assert np.array_equal(sc[:1024], E.astype(np.int64) @ q.astype(np.int64)) and np.all(sc[1024:] == 0)

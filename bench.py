@@ -298,7 +298,10 @@ def main():
     dom = max(kern, key=lambda k: kern[k]["total_ms"])
     roof = None
     if dom in work:
-        achieved = work[dom] / (kern[dom]["total_ms"] / 1e3)
+        # waves overlap on two streams, so a kernel's event time includes time
+        # shared with the other stream's kernels: attribute the step time to
+        # kernels by their share of the summed event time
+        achieved = work[dom] / (kern[dom]["share"] * ms_step * args.steps / 1e3)
         peak = peaks["mac128_per_s"] if dom == "mac" else peaks["butterfly_per_s"]
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
                 "unit": "Gmodmul/s", "frac": achieved / peak, "traffic": None,

@@ -82,6 +82,8 @@ typedef struct {
     uint64_t total_chunks;           /* sum over clusters of their chunk counts */
     uint64_t cluster_bytes;          /* device bytes of the encoded clusters */
     uint32_t max_wave;
+    uint32_t drop_c0, drop_c1;       /* low bits dropped from c0 / c1 of a compressed response */
+    uint64_t compressed_bytes;       /* bytes of one compressed response ciphertext */
 } wally_info;
 
 /* Derive primes, roots and NTT tables for `params` on `params->device` and
@@ -133,10 +135,13 @@ int wally_export_cluster(wally_ctx *ctx, uint32_t cluster_id, uint64_t *out, voi
  *   out          device uint64_t [sum m][2][L][N], coefficient form, residues in [0, q_l)
  * Asynchronous on `stream`: queries are grouped by cluster on the device and
  * evaluated in waves of at most max_wave queries in scratch memory the
- * context owns (allocated on first use, grown when needed).  Queries with an
- * out-of-range cluster id produce no output and make wally_sync return
+ * context owns (allocated on first use, grown when needed).  Consecutive
+ * waves alternate between lanes 0 and 1 (see wally_eval_batch_lane), the odd
+ * ones on a second stream of the context that forks from `stream` and joins
+ * back into it before the call's work is complete on `stream`.  Queries with
+ * an out-of-range cluster id produce no output and make wally_sync return
  * WALLY_EINVAL.  Calls on one context must not overlap (the scratch is
- * shared); use one context per concurrent stream.
+ * shared), nor with wally_eval_batch_lane on lanes 0 or 1.
  * Errors: WALLY_EINVAL, WALLY_ESTATE (no clusters), WALLY_ENOMEM, WALLY_ECUDA. */
 int wally_eval_batch(wally_ctx *ctx, uint32_t n, const uint32_t *cluster_ids, const uint64_t *cts,
                      const uint64_t *galois_keys, const uint32_t *input_index, const uint64_t *out_offsets,
@@ -190,6 +195,25 @@ int wally_rotate_noalloc(wally_ctx *ctx, uint32_t n, uint64_t galois_elt, const 
 /* Wait for `stream` and report the first device-side error recorded since
  * the previous wally_sync (and clear it). */
 int wally_sync(wally_ctx *ctx, void *stream);
+
+/* Response compression (Sec. 7 "Reducing the response size"): every score
+ * ciphertext (device, [n][2][L][N], coefficient form, as wally_eval_batch
+ * writes it) is switched to its last limb q' = q_{L-1} by a chain of exact
+ * rescalings by q_0, ..., q_{L-2} (each replaces c by round(c / q_i), via the
+ * centred residue mod q_i), then l0 = floor(log2(q'/t) - 2) low bits of c0
+ * and l1 = floor(log2(q'/t) - 2 - log2(8 sqrt(2N/9))) of c1 are dropped with
+ * rounding to nearest (wally_info.drop_c0 / drop_c1).  Each group of 8
+ * coefficients packs into b bytes (b bits a value, little-endian bits),
+ * component 0 then 1: out (device) [n][wally_info.compressed_bytes].
+ * Asynchronous on `stream`. */
+int wally_compress_responses(wally_ctx *ctx, uint32_t n, const uint64_t *cts, uint8_t *out, void *stream);
+
+/* Client side: decrypt compressed responses (device [n][compressed_bytes])
+ * with x = c0'' 2^l0 + c1'' 2^l1 s (mod q'), m = round(t x / q') mod t, and
+ * decode the slots: scores device int64_t [n][N], centred; response i uses
+ * secret[secret_index ? secret_index[i] : i]. */
+int wally_decrypt_compressed(wally_ctx *ctx, uint32_t n, const int8_t *secret, const uint32_t *secret_index,
+                             const uint8_t *packed, int64_t *scores, void *stream);
 
 /* ---------------------------------------------------------------- measurement
  * Per-launch device time of the evaluation kernels, taken with CUDA events

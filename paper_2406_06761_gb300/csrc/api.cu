@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cmath>
 #include <string>
 #include <vector>
 #include <algorithm>
@@ -154,6 +155,7 @@ struct wally_ctx {
     uint32_t N = 0, log_n = 0, L = 0, d = 0, d_pad = 0, g = 0, h = 0;
     std::vector<uint64_t> mods;  // q_0..q_{L-1}, P, t
     uint64_t zeta_t = 0, k1 = 0, kg = 0, k1_inv = 0, kg_inv = 0;
+    uint32_t drop0 = 0, drop1 = 0, bits0 = 0, bits1 = 0;  // response compression
     uint32_t max_wave = 1024;
     DevParams dp{};
     DevParams *d_dp = nullptr;
@@ -170,6 +172,9 @@ struct wally_ctx {
 
     // evaluation workspaces
     Lane lanes[WALLY_MAX_LANES];
+    // second stream of wally_eval_batch (waves alternate between lanes 0, 1)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // host-buffer path staging
     DevBuf<u64> stage_ct[2], stage_key[2], stage_out[2];
     DevBuf<u32> stage_cluster[2];
@@ -249,6 +254,10 @@ int setup_tables(wally_ctx *c)
             if (i != j) qhat = mulmod_h(qhat, c->mods[i] % q, q);
         dp.theta[j] = invmod_h(qhat, q);
         dp.theta_s[j] = shoup_of(dp.theta[j], q);
+        for (uint32_t i = 0; i < c->L; i++) {
+            dp.rs_inv[i][j] = i == j ? 0 : invmod_h(c->mods[i] % q, q);
+            dp.rs_inv_s[i][j] = shoup_of(dp.rs_inv[i][j], q);
+        }
     }
     // slot s = rho*N/2 + col is the evaluation at zeta^(+-3^col); the NTT
     // keeps the evaluation at zeta^(2 brv(i) + 1) in position i.
@@ -501,6 +510,23 @@ int wally_setup_params(const wally_params *prm, wally_ctx **out)
     c->k1_inv = inv_mod_2n(c->k1, step);
     c->kg_inv = inv_mod_2n(c->kg, step);
     c->max_wave = prm->max_wave ? prm->max_wave : 1024;
+    {
+        // response compression (Sec. 7): l0 = floor(log2(q'/t) - 2),
+        // l1 = floor(log2(q'/t) - 2 - log2(z sqrt(2n/9))), z = 8
+        const double r = std::log2((double)c->mods[c->L - 1] / (double)c->mods[c->L + 1]);
+        const double l0 = std::floor(r - 2), l1 = std::floor(r - 2 - std::log2(8.0 * std::sqrt(2.0 * c->N / 9.0)));
+        c->drop0 = l0 > 0 ? (uint32_t)l0 : 0;
+        c->drop1 = l1 > 0 ? (uint32_t)l1 : 0;
+        const uint64_t q = c->mods[c->L - 1];
+        auto bits = [&](uint32_t l) {
+            uint64_t mx = (q - 1 + (l ? (1ull << (l - 1)) : 0)) >> l;
+            uint32_t b = 0;
+            while (mx) { b++; mx >>= 1; }
+            return b;
+        };
+        c->bits0 = bits(c->drop0);
+        c->bits1 = bits(c->drop1);
+    }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     int rc = setup_tables(c);
     if (rc != WALLY_OK) {
@@ -525,6 +551,9 @@ void wally_destroy(wally_ctx *c)
     c->d_chunks.release();
     c->d_chunk0.release();
     for (Lane &ln : c->lanes) ln.release();
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
     for (int b = 0; b < 2; b++) {
         c->stage_ct[b].release();
         c->stage_key[b].release();
@@ -559,6 +588,9 @@ int wally_query_info(const wally_ctx *c, wally_info *o)
     o->total_chunks = c->total_chunks;
     o->cluster_bytes = c->ptxt.n * 8;
     o->max_wave = c->max_wave;
+    o->drop_c0 = c->drop0;
+    o->drop_c1 = c->drop1;
+    o->compressed_bytes = (uint64_t)(c->N / 8) * (c->bits0 + c->bits1);
     return WALLY_OK;
 }
 
@@ -691,10 +723,50 @@ int wally_eval_batch_lane(wally_ctx *c, uint32_t lane, uint32_t n, const uint32_
     return WALLY_OK;
 }
 
+// Waves alternate between lane 0 on the caller's stream and lane 1 on the
+// context's second stream (forked from and joined back into the caller's
+// stream with events), so that one wave's kernels fill the tails and the
+// memory-bound phases of the other's.
 int wally_eval_batch(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
                      const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out, void *stream)
 {
-    return wally_eval_batch_lane(c, 0, n, ids, cts, keys, input_index, out_offsets, out, stream);
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n <= c->max_wave) return wally_eval_batch_lane(c, 0, n, ids, cts, keys, input_index, out_offsets, out, stream);
+    if (!c->num_clusters) return fail(WALLY_ESTATE, "no clusters loaded");
+    if (!ids || !cts || !keys || !out_offsets || !out) return fail(WALLY_EINVAL, "null argument");
+    if (!aligned16(cts) || !aligned16(keys) || !aligned16(out)) return fail(WALLY_EINVAL, "buffers must be 16-byte aligned");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->side) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    }
+    const uint32_t W = c->max_wave, K = c->num_clusters;
+    Lane &l0 = c->lanes[0], &l1 = c->lanes[1];
+    int rc = ensure_workspace(c, l0, W, c->m_max);
+    if (rc == WALLY_OK) rc = ensure_workspace(c, l1, W, c->m_max);
+    if (rc) return rc;
+    if (l0.counts.ensure(K) != cudaSuccess || l0.cstart.ensure(K + 1) != cudaSuccess ||
+        l0.fill.ensure(K) != cudaSuccess || l0.sorted_q.ensure(n) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the grouping arrays");
+    // a0: group by cluster (shared by both lanes)
+    CUDA_TRY(launch_group(ids, n, K, l0.counts.p, l0.cstart.p, l0.fill.p, l0.sorted_q.p, c->d_err, st));
+    CUDA_TRY(cudaEventRecord(c->fork_ev, st));
+    CUDA_TRY(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+    uint32_t w = 0;
+    for (uint32_t wb = 0; wb < n; wb += W, w++) {
+        const uint32_t len = std::min(W, n - wb);
+        Lane &ln = (w & 1) ? l1 : l0;
+        cudaStream_t s = (w & 1) ? c->side : st;
+        CUDA_TRY(launch_gather_wave(ln.wp, l0.sorted_q.p, ids, l0.cstart.p, K, wb, len, cts, keys, input_index,
+                                    out_offsets, out, c->ctw(), c->keysw(), s));
+        rc = run_wave(c, ln, ln.wp, len, s);
+        if (rc) return rc;
+    }
+    CUDA_TRY(cudaEventRecord(c->join_ev, c->side));
+    CUDA_TRY(cudaStreamWaitEvent(st, c->join_ev, 0));
+    return WALLY_OK;
 }
 
 int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
@@ -903,6 +975,29 @@ int wally_profile_read(wally_ctx *c, wally_kernel_time *out, uint32_t cap, uint3
         n++;
     }
     *count = n;
+    return WALLY_OK;
+}
+
+int wally_compress_responses(wally_ctx *c, uint32_t n, const uint64_t *cts, uint8_t *out, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0) return WALLY_OK;
+    if (!cts || !out) return fail(WALLY_EINVAL, "null argument");
+    if (c->bits0 > 57 || c->bits1 > 57) return fail(WALLY_EINVAL, "response limb too wide to pack");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(launch_compress(c->dp, cts, n, out, c->drop0, c->drop1, c->bits0, c->bits1, (cudaStream_t)stream));
+    return WALLY_OK;
+}
+
+int wally_decrypt_compressed(wally_ctx *c, uint32_t n, const int8_t *secret, const uint32_t *secret_index,
+                             const uint8_t *packed, int64_t *scores, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0) return WALLY_OK;
+    if (!secret || !packed || !scores) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(launch_decrypt_compressed(c->dp, secret, secret_index, packed, n, c->drop0, c->drop1, c->bits0,
+                                       c->bits1, scores, (cudaStream_t)stream));
     return WALLY_OK;
 }
 

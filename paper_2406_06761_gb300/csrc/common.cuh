@@ -54,6 +54,8 @@ struct DevParams {
     u64 pmodq[WALLY_MAX_LIMBS], pmodq_s[WALLY_MAX_LIMBS];  // P mod q_j
     u64 delta[WALLY_MAX_LIMBS], delta_s[WALLY_MAX_LIMBS];  // [floor(Q/t)]_{q_j}
     u64 theta[WALLY_MAX_LIMBS], theta_s[WALLY_MAX_LIMBS];  // [(Q/q_j)^-1]_{q_j}
+    u64 rs_inv[WALLY_MAX_LIMBS][WALLY_MAX_LIMBS];             // q_i^-1 mod q_j (response switch)
+    u64 rs_inv_s[WALLY_MAX_LIMBS][WALLY_MAX_LIMBS];
     const u32 *slot_pos;      // [N] NTT position (mod t) of slot s
     const DevParams *self;    // device copy of this block (kernels read it there)
 };

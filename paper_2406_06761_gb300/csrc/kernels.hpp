@@ -114,6 +114,12 @@ cudaError_t launch_encrypt(const DevParams &dp, const int8_t *secret, const u64 
                            const int8_t *enc_e, u32 n, u64 *cts, cudaStream_t st);
 cudaError_t launch_keygen(const DevParams &dp, const int8_t *secret, const u64 *key_a, const int8_t *key_e, u32 n,
                           u64 k1, u64 kg, u64 k1_inv, u64 kg_inv, u64 *keys, cudaStream_t st);
+// Response compression (switch to the last limb, drop low bits, pack).
+cudaError_t launch_compress(const DevParams &dp, const u64 *cts, u32 n, uint8_t *out, u32 l0, u32 l1, u32 b0, u32 b1,
+                            cudaStream_t st);
+cudaError_t launch_decrypt_compressed(const DevParams &dp, const int8_t *secret, const u32 *secret_index,
+                                      const uint8_t *packed, u32 n, u32 l0, u32 l1, u32 b0, u32 b1, int64_t *scores,
+                                      cudaStream_t st);
 cudaError_t launch_decrypt(const DevParams &dp, const int8_t *secret, const u32 *secret_index, const u64 *cts, u32 n,
                            u64 *xs, int64_t *scores, cudaStream_t st);
 

@@ -9,6 +9,8 @@ namespace wally {
 
 namespace {
 
+typedef unsigned char u8_t;
+
 
 __device__ __forceinline__ void load_mod(Mod *s, const DevParams *dpp, int j)
 {
@@ -335,6 +337,122 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u6
     }
 }
 
+// ---------------------------------------------------------------- response compression
+// Sec. 7 "Reducing the response size".  Per coefficient of both components:
+// the chain of exact rescalings by q_0, ..., q_{L-2} (each step replaces c by
+// round(c / q_i) = (c - centred [c]_{q_i}) * q_i^-1 on the remaining limbs),
+// leaving the residue mod q' = q_{L-1}; then l low bits dropped with rounding
+// to nearest.  Each group of 8 coefficients packs into b bytes (b bits each,
+// little-endian bit order); component 0 then component 1.
+__device__ __forceinline__ u64 switch_to_last_limb(const DevParams *dpp, const u64 *ct_c, int n, int N, int L)
+{
+    u64 v[WALLY_MAX_LIMBS];
+    for (int j = 0; j < L; j++) v[j] = ct_c[(size_t)j * N + n];
+    for (int i = 0; i + 1 < L; i++) {
+        const u64 qi = dpp->m[i].p, r = v[i];
+        const bool neg = r > (qi - 1) / 2;
+        for (int j = i + 1; j < L; j++) {
+            const u64 qj = dpp->m[j].p;
+            // centred remainder mod q_j: |r_c| < q_i / 2 < q_j (primes of one size)
+            const u64 rm = neg ? qj - (qi - r) : r;
+            v[j] = csub(shoup_mul(v[j] + qj - rm, dpp->rs_inv[i][j], dpp->rs_inv_s[i][j], qj), qj);
+        }
+    }
+    return v[L - 1];
+}
+
+__global__ void __launch_bounds__(256) k_compress(const DevParams *dpp, const u64 *cts, u8_t *out, u32 l0, u32 l1,
+                                                  u32 b0, u32 b1)
+{
+    const int L = dpp->L, N = dpp->n;
+    const u32 x = blockIdx.x;
+    const u64 *ct = cts + (size_t)x * 2 * L * N;
+    u8_t *o = out + (size_t)x * (N / 8) * (b0 + b1);
+    for (int c = 0; c < 2; c++) {
+        const u32 l = c ? l1 : l0, b = c ? b1 : b0;
+        u8_t *base = o + (c ? (size_t)(N / 8) * b0 : 0);
+        for (int g = threadIdx.x; g < N / 8; g += blockDim.x) {
+            u64 buf = 0;
+            int nb = 0;
+            u8_t *dst = base + (size_t)g * b;
+            for (int k = 0; k < 8; k++) {
+                const u64 xv = switch_to_last_limb(dpp, ct + (size_t)c * L * N, 8 * g + k, N, L);
+                const u64 val = l ? (xv + (1ull << (l - 1))) >> l : xv;
+                buf |= val << nb;
+                nb += b;
+                while (nb >= 8) {  // fewer than 8 bits stay pending, so b <= 57 fits
+                    *dst++ = (u8_t)buf;
+                    buf >>= 8;
+                    nb -= 8;
+                }
+            }
+            // 8 values of b bits are exactly b bytes: nothing is left pending
+        }
+    }
+}
+
+// Value e (b bits) of a packed component.
+__device__ __forceinline__ u64 unpack_at(const u8_t *base, int e, u32 b)
+{
+    const u64 bit = (u64)e * b;
+    const u8_t *p = base + (bit >> 3);
+    const int sh = (int)(bit & 7);
+    const int nbytes = (sh + (int)b + 7) >> 3;
+    u64 lo = 0, hi = 0;
+    for (int i = 0; i < nbytes && i < 8; i++) lo |= (u64)p[i] << (8 * i);
+    if (nbytes > 8) hi = p[8];
+    u64 v = lo >> sh;
+    if (sh) v |= hi << (64 - sh);
+    return b >= 64 ? v : (v & ((1ull << b) - 1));
+}
+
+// CTA (response n): x = c0'' 2^l0 + c1'' 2^l1 s (mod q'), m = round(t x / q')
+// mod t, slots decoded and centred.
+template <int LOGN>
+__global__ void NTT_LB_WIDE(LOGN) k_decrypt_compressed(const DevParams *dpp, const int8_t *secret,
+                                                       const u32 *secret_index, const u8_t *packed, u32 l0, u32 l1,
+                                                       u32 b0, u32 b1, int64_t *scores)
+{
+    constexpr int N = 1 << LOGN, T = N / 32;
+    extern __shared__ u64 sm[];
+    Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
+    Tw *twi = twf;  // one cache, reloaded by every transform
+    __shared__ Mod md;
+    const u32 n = blockIdx.x;
+    const int L = dpp->L;
+    load_mod(&md, dpp, L - 1);
+    const u64 q = md.p;
+    const u32 si = secret_index ? secret_index[n] : n;
+    u64 sv[32];
+    secret_ntt<LOGN>(sm, sv, secret + (size_t)si * N, md, twf);
+    const u8_t *p0 = packed + (size_t)n * (N / 8) * (b0 + b1);
+    const u8_t *p1 = p0 + (size_t)(N / 8) * b0;
+    const u64 f1 = ((u64)1 << l1) % q, f0 = ((u64)1 << l0) % q;
+    const u64 f1s = (u64)(((unsigned __int128)f1 << 64) / q), f0s = (u64)(((unsigned __int128)f0 << 64) / q);
+#pragma unroll 4
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        sm[spos(e)] = csub(shoup_mul(unpack_at(p1, e, b1), f1, f1s, q), q);
+    }
+    poly_times_secret<LOGN>(sm, sv, md, twf, twi);
+    const u64 t = dpp->m[L + 1].p;
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        const u64 c0 = csub(shoup_mul(unpack_at(p0, e, b0), f0, f0s, q), q);
+        const u64 xv = addmod(c0, inv_finish(sm[spos(e)], md), q);
+        sv[u] = (u64)((((unsigned __int128)t * xv) + q / 2) / q) % t;
+    }
+    __syncthreads();
+    load_mod(&md, dpp, L + 1);
+    for (int u = 0; u < 32; u++) sm[spos(threadIdx.x + T * u)] = sv[u];
+    ntt_fwd<LOGN>(sm, twf, md);
+    for (int u = 0; u < 32; u++) {
+        const int s = threadIdx.x + T * u;
+        const u64 v = fwd_finish(sm[spos(dpp->slot_pos[s])], md);
+        scores[(size_t)n * N + s] = v > t / 2 ? (int64_t)v - (int64_t)t : (int64_t)v;
+    }
+}
+
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes)
 {
@@ -354,6 +472,7 @@ cudaError_t set_attrs_logn()
     SA(k_keygen);
     SA(k_decrypt_residues);
     SA(k_decrypt_scale);
+    SA(k_decrypt_compressed);
 #undef SA
     return e;
 }
@@ -443,4 +562,25 @@ cudaError_t launch_decrypt(const DevParams &dp, const int8_t *secret, const u32 
     return cudaGetLastError();
 }
 
+}  // namespace wally
+
+namespace wally {
+cudaError_t launch_compress(const DevParams &dp, const u64 *cts, u32 n, uint8_t *out, u32 l0, u32 l1, u32 b0, u32 b1,
+                            cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_compress<<<n, 256, 0, st>>>(dp.self, cts, out, l0, l1, b0, b1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decrypt_compressed(const DevParams &dp, const int8_t *secret, const u32 *secret_index,
+                                      const uint8_t *packed, u32 n, u32 l0, u32 l1, u32 b0, u32 b1, int64_t *scores,
+                                      cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const DevParams *dpp = dp.self;
+    DISPATCH_LOGN(dp.log_n, (k_decrypt_compressed<LG><<<n, ntt_threads(LG), smem_bytes(LG), st>>>(
+                                dpp, secret, secret_index, packed, l0, l1, b0, b1, scores)));
+    return cudaGetLastError();
+}
 }  // namespace wally

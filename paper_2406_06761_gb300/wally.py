@@ -42,7 +42,8 @@ class wally_info(ctypes.Structure):
         ("p_special", ctypes.c_uint64), ("t", ctypes.c_uint64), ("zeta_t", ctypes.c_uint64),
         ("k1", ctypes.c_uint64), ("kg", ctypes.c_uint64), ("ct_words", ctypes.c_uint64),
         ("keys_words", ctypes.c_uint64), ("total_chunks", ctypes.c_uint64), ("cluster_bytes", ctypes.c_uint64),
-        ("max_wave", ctypes.c_uint32),
+        ("max_wave", ctypes.c_uint32), ("drop_c0", ctypes.c_uint32), ("drop_c1", ctypes.c_uint32),
+        ("compressed_bytes", ctypes.c_uint64),
     ]
 
 
@@ -71,6 +72,8 @@ SIGNATURES = {
     "wally_keygen": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "wally_encrypt_query": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "wally_decrypt_scores": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
+    "wally_compress_responses": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp]),
+    "wally_decrypt_compressed": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "wally_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "wally_profile_read": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_u32)]),
     "wally_measure_int_peaks": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
@@ -232,6 +235,18 @@ def wally_decrypt_scores(ctx: int, n: int, secret, secret_index, cts, scores, st
     _require_cuda(secret, secret_index, cts, scores)
     _check(load().wally_decrypt_scores(ctx, n, _ptr(secret), _ptr(secret_index), _ptr(cts), _ptr(scores),
                                        _stream(stream)))
+
+
+def wally_compress_responses(ctx: int, n: int, cts, out, stream=None) -> None:
+    """out: uint8 device tensor [n][compressed_bytes]."""
+    _require_cuda(cts, out)
+    _check(load().wally_compress_responses(ctx, n, _ptr(cts), _ptr(out), _stream(stream)))
+
+
+def wally_decrypt_compressed(ctx: int, n: int, secret, secret_index, packed, scores, stream=None) -> None:
+    _require_cuda(secret, secret_index, packed, scores)
+    _check(load().wally_decrypt_compressed(ctx, n, _ptr(secret), _ptr(secret_index), _ptr(packed), _ptr(scores),
+                                           _stream(stream)))
 
 
 def wally_profile_enable(ctx: int, enable: bool = True) -> None:

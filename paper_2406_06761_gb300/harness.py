@@ -13,6 +13,7 @@ buffer; every query of the batch is still evaluated and written out.
 from __future__ import annotations
 
 import dataclasses
+import sys
 
 import numpy as np
 import torch
@@ -61,7 +62,7 @@ class DeviceWorkload:
 
     def _log(self, msg):
         if self.verbose:
-            print(f"[workload] {msg}", flush=True)
+            print(f"[workload] {msg}", file=sys.stderr, flush=True)
 
     # -------------------------------------------------------------- pool
     def entry_randomness(self, e: int) -> W.ClientRandomness:

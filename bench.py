@@ -348,6 +348,24 @@ def main():
                "achieved_GBps": value / world * alg_bytes_q / 1e9,
                "peak_GBps": 6790.0, "frac_of_measured_hbm": value / world * alg_bytes_q / 1e9 / 6790.0}
 
+    # the plain one-query-at-a-time GPU path: each query its own call, waited for
+    single = None
+    if rank == 0:
+        one = []
+        for qi in range(0, min(n, 200)):
+            b = wl.device_batch(qi, qi + 1)
+            o1 = wl.alloc_out(b[3]) if qi == 0 or b[3] > o1.shape[0] else o1
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            wl.eval(b, o1[:b[3]], stream)
+            torch.cuda.synchronize(dev)
+            one.append(time.perf_counter() - t0)
+        one = np.array(one[5:])
+        single = {"value": 1.0 / float(one.mean()), "unit": "queries/s", "latency_ms_p50": float(np.median(one) * 1e3),
+                  "latency_ms_p99": float(np.percentile(one, 99) * 1e3), "queries": int(len(one)),
+                  "note": "one query per wally_eval_batch call, synchronised"}
+        log("one query at a time", single)
+
     # end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -379,6 +397,7 @@ def main():
         "int_peaks": peaks,
         "clocks": clk,
         "e2e": e2e,
+        "one_query_path": single,
         "cpu_baseline": cpu,
     }
     if rank == 0:

@@ -387,7 +387,9 @@ def main():
         "config": {"workload": args.workload, "queries": n, "real_queries": n_real, "clusters": int(len(wl.sizes)),
                    "embeddings": int(wl.sizes.sum()), "N": N, "L": L, "d": info.dim, "g": g, "h": h,
                    "client_pool": wl.pool_size, "sub_batches": len(subs), "max_wave": int(info.max_wave),
-                   "l2": "inputs larger than L2 (91 GB database, client pool > 129 MB); no flush"},
+                   "store": "compact" if info.store == Wl.STORE_COMPACT else "ntt",
+                   "l2": f"inputs larger than L2 ({info.cluster_bytes / 1e9:.1f} GB cluster store, "
+                         f"{wl.pool_size * (wl.ctw + wl.keysw) * 8 / 1e9:.1f} GB client pool); no flush"},
         "real_qps": world * n_real / (ms_step / 1e3),
         "latency_ms": {"p50": p50, "p99": p99, "note": "completion time of the query's sub-batch within a step"},
         "gpu_launches": int(sum(v[0] for v in prof.values()) / args.steps),

@@ -69,7 +69,27 @@ typedef struct {
     uint64_t p_special;    /* optional explicit P, 0 = derive */
     uint64_t t;            /* optional explicit t, 0 = derive */
     uint32_t max_wave;     /* queries per internal wave of wally_eval_batch, 0 = 1024 */
+    uint32_t store;        /* cluster store: WALLY_STORE_AUTO / _NTT / _COMPACT (below) */
+    uint32_t cache_chunks; /* compact store: encoded chunks held per lane, 0 = 16 */
 } wally_params;
+
+/* How wally_load_clusters keeps the clusters.
+ *  WALLY_STORE_NTT: every chunk's g*h plaintexts encoded, in NTT form, resident
+ *    (d_pad * L * N * 8 bytes a chunk: 50 MB at N = 8192, L = 3, d_pad = 256;
+ *    805 MB at N = 16384, L = 6, d_pad = 1024).
+ *  WALLY_STORE_COMPACT: only the int8 embeddings are resident (d bytes a row);
+ *    each wave encodes the chunks its queries name (the same kernel and the
+ *    same bits as the NTT store) into a per-lane cache of cache_chunks chunks
+ *    right before its multiply-accumulate.  Waves then also end where their
+ *    clusters would need more than cache_chunks chunks, and the evaluation
+ *    reads the per-cluster query counts back once per call (one host
+ *    synchronisation of `stream`).  For databases whose encoded form exceeds
+ *    device memory (1 M x 768 at N = 16384: 805 GB encoded, 768 MB as int8).
+ *  WALLY_STORE_AUTO: NTT if the encoded clusters take at most 60 % of the
+ *    free device memory when they are loaded, else COMPACT. */
+#define WALLY_STORE_AUTO 0u
+#define WALLY_STORE_NTT 1u
+#define WALLY_STORE_COMPACT 2u
 
 typedef struct {
     uint32_t n, log_n, num_q, dim, d_pad, g, h;
@@ -84,6 +104,8 @@ typedef struct {
     uint32_t max_wave;
     uint32_t drop_c0, drop_c1;       /* low bits dropped from c0 / c1 of a compressed response */
     uint64_t compressed_bytes;       /* bytes of one compressed response ciphertext */
+    uint32_t store;                  /* WALLY_STORE_NTT or _COMPACT once clusters are loaded, else the request */
+    uint32_t cache_chunks;           /* compact store: chunks per lane cache */
 } wally_info;
 
 /* Derive primes, roots and NTT tables for `params` on `params->device` and
@@ -98,7 +120,7 @@ int wally_query_info(const wally_ctx *ctx, wally_info *out);
 
 /* Server initialisation (Alg. "Server Initialization", Sec. 5): encode every
  * cluster into its plaintext set and keep it resident in device memory in NTT
- * form.  Cluster c has sizes[c] embeddings (rows of `embeddings`, host, int8
+ * form (or keep the embeddings and encode per wave: WALLY_STORE_COMPACT).  Cluster c has sizes[c] embeddings (rows of `embeddings`, host, int8
  * [sum sizes][dim], clusters back to back in id order).  Per cluster,
  * m = max(1, ceil(size/N)) chunks of g*h plaintexts; chunk k, slot
  * s = beta*d_pad + x holds embedding k*N + s, and plaintext (i, b) is diagonal
@@ -223,7 +245,7 @@ int wally_decrypt_compressed(wally_ctx *ctx, uint32_t n, const int8_t *secret, c
  * launches and milliseconds per kernel kind into out[0 .. *count) (at most
  * cap entries) and clears the collection. */
 typedef struct {
-    char name[16];       /* to_ntt, ks_a, ks_b, ks_c, mac, output, plan */
+    char name[16];       /* to_ntt, ks_a, ks_b, ks_c, mac, output, plan, encode (compact store) */
     uint64_t launches;
     double total_ms;
 } wally_kernel_time;

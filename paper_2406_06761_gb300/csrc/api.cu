@@ -75,6 +75,30 @@ struct DevBuf {
     }
 };
 
+// Pinned host memory (asynchronous copies), grown on demand.
+template <typename T>
+struct PinnedBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t count)
+    {
+        if (count <= n) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMallocHost((void **)&p, sizeof(T) * (count ? count : 1));
+        if (e == cudaSuccess) n = count;
+        else p = nullptr;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
 // Per-launch CUDA events, summed per kernel kind when read.
 struct EventProfiler : Profiler {
     std::vector<cudaEvent_t> pool;
@@ -127,8 +151,21 @@ struct Lane {
     WavePlan wp{};
     // batch grouping
     DevBuf<u32> counts, cstart, fill, sorted_q;
+    // compact cluster store: the chunks of the running wave, encoded, and
+    // per cluster the cache index of its chunk 0
+    DevBuf<u64> cache;
+    DevBuf<u32> wchunk0, zlist;
+    PinnedBuf<u32> h_counts, h_zlist;
+    cudaEvent_t zlist_ev = nullptr;  // the last upload of h_zlist
     void release()
     {
+        cache.release();
+        wchunk0.release();
+        zlist.release();
+        h_counts.release();
+        h_zlist.release();
+        if (zlist_ev) cudaEventDestroy(zlist_ev);
+        zlist_ev = nullptr;
         keysN.release();
         ctp.release();
         T.release();
@@ -157,6 +194,7 @@ struct wally_ctx {
     uint64_t zeta_t = 0, k1 = 0, kg = 0, k1_inv = 0, kg_inv = 0;
     uint32_t drop0 = 0, drop1 = 0, bits0 = 0, bits1 = 0;  // response compression
     uint32_t max_wave = 1024;
+    uint32_t store_req = WALLY_STORE_AUTO, store = WALLY_STORE_NTT, cache_chunks = 16;
     DevParams dp{};
     DevParams *d_dp = nullptr;
     std::vector<void *> tables;
@@ -169,6 +207,10 @@ struct wally_ctx {
     std::vector<uint32_t> h_chunks, h_chunk0;
     DevBuf<u64> ptxt;
     DevBuf<u32> d_chunks, d_chunk0;
+    // compact store: the embeddings and their cluster index stay resident
+    DevBuf<int8_t> emb;
+    DevBuf<u64> row0;
+    DevBuf<u32> csize, d_cc, d_ck;
 
     // evaluation workspaces
     Lane lanes[WALLY_MAX_LANES];
@@ -179,14 +221,17 @@ struct wally_ctx {
     DevBuf<u64> stage_ct[2], stage_key[2], stage_out[2];
     DevBuf<u32> stage_cluster[2];
     DevBuf<void *> stage_ptrs[2];
-    // client temporaries
+    // client and export temporaries
     DevBuf<u64> tmp;
+    DevBuf<u32> tmp32;
     // optional per-launch timing
     bool prof_on = false;
     EventProfiler prof;
     Profiler *pr() { return prof_on ? &prof : nullptr; }
 
     size_t ctw() const { return (size_t)2 * L * N; }
+    size_t chunk_words() const { return (size_t)L * N * d_pad; }
+    bool compact() const { return store == WALLY_STORE_COMPACT; }
     size_t keysw() const { return (size_t)2 * L * 2 * (L + 1) * N; }
 };
 
@@ -367,7 +412,7 @@ RotArgs rot_args(Lane &ln)
 
 // Steps a1-a5 for one wave whose plan inputs (counts[0], cluster, src_ct,
 // src_key, dst_out of wp) are already on the device, in stream order.
-int run_wave(wally_ctx *c, Lane &ln, const WavePlan &wp, uint32_t wave_len, cudaStream_t st)
+int run_wave(wally_ctx *c, Lane &ln, const WavePlan &wp, uint32_t wave_len, const ClusterStore &cs, cudaStream_t st)
 {
     const DevParams &dp = c->dp;
     const size_t ctw = c->ctw(), keysw = c->keysw();
@@ -395,7 +440,7 @@ int run_wave(wally_ctx *c, Lane &ln, const WavePlan &wp, uint32_t wave_len, cuda
         CUDA_TRY(launch_rotate(dp, a, st, c->pr()));
     }
     // a3: T_i = sum_b P'_{k,i,b} ct'[b]
-    CUDA_TRY(launch_mac(dp, cluster_store(c), wp, ln.ctp.p, ln.T.p, wave_len, c->m_max, c->num_sms, st, c->pr()));
+    CUDA_TRY(launch_mac(dp, cs, wp, ln.ctp.p, ln.T.p, wave_len, c->m_max, c->num_sms, st, c->pr()));
     // a4: S = T_{h-1}; S = Rot_g(S) + T_i, i = h-2 .. 0
     const uint32_t np_max = wave_len * c->m_max;
     for (int i = (int)h - 2; i >= 0; i--) {
@@ -424,6 +469,170 @@ int run_wave(wally_ctx *c, Lane &ln, const WavePlan &wp, uint32_t wave_len, cuda
     // a5: back to coefficient form, into the caller's output
     if (h == 1) CUDA_TRY(launch_output(dp, wp, ln.T.p, ctw, np_max, st, c->pr()));
     else CUDA_TRY(launch_output(dp, wp, ln.S.p, ctw, np_max, st, c->pr()));
+    return WALLY_OK;
+}
+
+// ---------------------------------------------------------------- compact cluster store
+// One wave of a call: positions [begin, begin + len) of the cluster-sorted
+// order and, with the compact store, the nz chunks (list entries z_off ..)
+// that its queries name.
+struct Wave {
+    uint32_t begin, len, z_off, nz;
+};
+
+// Fixed waves of at most W positions (the NTT store).
+void fixed_waves(uint32_t n, uint32_t W, std::vector<Wave> &waves)
+{
+    waves.clear();
+    for (uint32_t wb = 0; wb < n; wb += W) waves.push_back(Wave{wb, std::min(W, n - wb), 0, 0});
+}
+
+// Compact store: cluster k holds positions [start_k, start_k + cnt[k]) of the
+// sorted order (clusters in id order).  A wave ends at W queries or where
+// its clusters would need more than cache_chunks encoded chunks; a cluster
+// split between waves is encoded in each.  zc / zk: (cluster, chunk) of every
+// wave's chunks, a cluster's chunks consecutive.
+void compact_waves(const wally_ctx *c, const uint32_t *cnt, uint32_t W, std::vector<Wave> &waves,
+                   std::vector<uint32_t> &zc, std::vector<uint32_t> &zk)
+{
+    waves.clear();
+    zc.clear();
+    zk.clear();
+    const uint32_t C = c->cache_chunks;
+    uint32_t pos = 0;
+    Wave cur{0, 0, 0, 0};
+    for (uint32_t k = 0; k < c->num_clusters; k++) {
+        uint32_t rem = cnt[k];
+        const uint32_t m = c->h_chunks[k];
+        while (rem) {
+            if (cur.len == W || cur.nz + m > C) {
+                waves.push_back(cur);
+                cur = Wave{pos, 0, (uint32_t)zc.size(), 0};
+            }
+            const uint32_t take = std::min(rem, W - cur.len);
+            for (uint32_t j = 0; j < m; j++) {
+                zc.push_back(k);
+                zk.push_back(j);
+            }
+            cur.nz += m;
+            cur.len += take;
+            rem -= take;
+            pos += take;
+        }
+    }
+    if (cur.len) waves.push_back(cur);
+}
+
+// Copy the chunk lists to the device (ln.zlist: [2][total], clusters then
+// chunk indices) through the lane's pinned buffer, on `st`.
+int upload_chunk_list(Lane &ln, const std::vector<uint32_t> &zc, const std::vector<uint32_t> &zk, cudaStream_t st)
+{
+    const size_t tot = zc.size();
+    if (!ln.zlist_ev) CUDA_TRY(cudaEventCreateWithFlags(&ln.zlist_ev, cudaEventDisableTiming));
+    else CUDA_TRY(cudaEventSynchronize(ln.zlist_ev));  // the previous upload has read h_zlist
+    if (ln.h_zlist.ensure(2 * tot) != cudaSuccess || ln.zlist.ensure(2 * tot) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the chunk list");
+    if (!tot) return WALLY_OK;
+    memcpy(ln.h_zlist.p, zc.data(), 4 * tot);
+    memcpy(ln.h_zlist.p + tot, zk.data(), 4 * tot);
+    CUDA_TRY(cudaMemcpyAsync(ln.zlist.p, ln.h_zlist.p, 8 * tot, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaEventRecord(ln.zlist_ev, st));
+    return WALLY_OK;
+}
+
+int ensure_cache(wally_ctx *c, Lane &ln)
+{
+    if (ln.cache.ensure((size_t)c->cache_chunks * c->chunk_words()) != cudaSuccess ||
+        ln.wchunk0.ensure(std::max<uint32_t>(1, c->num_clusters)) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the chunk cache (%u chunks, %.2f GB)", c->cache_chunks,
+                    c->cache_chunks * (double)c->chunk_words() * 8 / 1e9);
+    return WALLY_OK;
+}
+
+// The cluster store a wave's multiply-accumulate reads: the resident NTT
+// store, or the lane's cache after encode_wave.
+ClusterStore wave_store(const wally_ctx *c, const Lane &ln)
+{
+    if (!c->compact()) return cluster_store(c);
+    ClusterStore cs;
+    cs.ptxt = ln.cache.p;
+    cs.chunk0 = ln.wchunk0.p;
+    cs.chunks = c->d_chunks.p;
+    cs.ts = c->ts;
+    return cs;
+}
+
+// Encode the wave's chunks (Alg. "Server Initialization", the same kernel as
+// the NTT store) into the lane's cache; zlist: the call's uploaded chunk list.
+int encode_wave(wally_ctx *c, Lane &ln, const Wave &w, const uint32_t *zlist, size_t total, cudaStream_t st)
+{
+    EncodeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.emb = c->emb.p;
+    a.row0 = c->row0.p;
+    a.size = c->csize.p;
+    a.chunk_cluster = zlist + w.z_off;
+    a.chunk_k = zlist + total + w.z_off;
+    a.total_chunks = w.nz;
+    a.ptxt = ln.cache.p;
+    a.ts = c->ts;
+    a.chunk0_out = ln.wchunk0.p;
+    CUDA_TRY(launch_encode_clusters(c->dp, a, st, c->pr()));
+    return WALLY_OK;
+}
+
+// Device-resident batch over nl lanes (1 or 2): group by cluster on lanes[0]
+// (on streams[0]), form the waves, and run them alternately on the lanes;
+// with two lanes the second stream forks from and joins back into the first.
+int eval_device(wally_ctx *c, Lane *const *lanes, const cudaStream_t *streams, int nl, uint32_t n, const uint32_t *ids,
+                const uint64_t *cts, const uint64_t *keys, const uint32_t *input_index, const uint64_t *out_offsets,
+                uint64_t *out)
+{
+    const uint32_t W = c->max_wave, K = c->num_clusters;
+    Lane &l0 = *lanes[0];
+    cudaStream_t st = streams[0];
+    for (int i = 0; i < nl; i++) {
+        int rc = ensure_workspace(c, *lanes[i], W, c->m_max);
+        if (rc == WALLY_OK && c->compact()) rc = ensure_cache(c, *lanes[i]);
+        if (rc) return rc;
+    }
+    if (l0.counts.ensure(K) != cudaSuccess || l0.cstart.ensure(K + 1) != cudaSuccess ||
+        l0.fill.ensure(K) != cudaSuccess || l0.sorted_q.ensure(n) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the grouping arrays");
+    // a0: group by cluster (shared by the lanes)
+    CUDA_TRY(launch_group(ids, n, K, l0.counts.p, l0.cstart.p, l0.fill.p, l0.sorted_q.p, c->d_err, st));
+    std::vector<Wave> waves;
+    std::vector<uint32_t> zc, zk;
+    if (c->compact()) {
+        if (l0.h_counts.ensure(K) != cudaSuccess) return fail(WALLY_ENOMEM, "cannot allocate the host counts");
+        CUDA_TRY(cudaMemcpyAsync(l0.h_counts.p, l0.counts.p, 4 * (size_t)K, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        compact_waves(c, l0.h_counts.p, W, waves, zc, zk);
+        int rc = upload_chunk_list(l0, zc, zk, st);
+        if (rc) return rc;
+    } else {
+        fixed_waves(n, W, waves);
+    }
+    if (waves.size() < 2) nl = 1;
+    if (nl > 1) {
+        CUDA_TRY(cudaEventRecord(c->fork_ev, st));
+        CUDA_TRY(cudaStreamWaitEvent(streams[1], c->fork_ev, 0));
+    }
+    for (size_t w = 0; w < waves.size(); w++) {
+        Lane &ln = *lanes[w % nl];
+        cudaStream_t s = streams[w % nl];
+        const Wave &wv = waves[w];
+        CUDA_TRY(launch_gather_wave(ln.wp, l0.sorted_q.p, ids, l0.cstart.p, K, wv.begin, wv.len, cts, keys,
+                                    input_index, out_offsets, out, c->ctw(), c->keysw(), s));
+        int rc = WALLY_OK;
+        if (c->compact()) rc = encode_wave(c, ln, wv, l0.zlist.p, zc.size(), s);
+        if (rc == WALLY_OK) rc = run_wave(c, ln, ln.wp, wv.len, wave_store(c, ln), s);
+        if (rc) return rc;
+    }
+    if (nl > 1) {
+        CUDA_TRY(cudaEventRecord(c->join_ev, streams[1]));
+        CUDA_TRY(cudaStreamWaitEvent(st, c->join_ev, 0));
+    }
     return WALLY_OK;
 }
 
@@ -510,6 +719,13 @@ int wally_setup_params(const wally_params *prm, wally_ctx **out)
     c->k1_inv = inv_mod_2n(c->k1, step);
     c->kg_inv = inv_mod_2n(c->kg, step);
     c->max_wave = prm->max_wave ? prm->max_wave : 1024;
+    if (prm->store > WALLY_STORE_COMPACT) {
+        delete c;
+        return fail(WALLY_EINVAL, "unknown cluster store %u", prm->store);
+    }
+    c->store_req = prm->store;
+    c->store = prm->store == WALLY_STORE_COMPACT ? WALLY_STORE_COMPACT : WALLY_STORE_NTT;
+    c->cache_chunks = prm->cache_chunks ? prm->cache_chunks : 16;
     {
         // response compression (Sec. 7): l0 = floor(log2(q'/t) - 2),
         // l1 = floor(log2(q'/t) - 2 - log2(z sqrt(2n/9))), z = 8
@@ -550,6 +766,11 @@ void wally_destroy(wally_ctx *c)
     c->ptxt.release();
     c->d_chunks.release();
     c->d_chunk0.release();
+    c->emb.release();
+    c->row0.release();
+    c->csize.release();
+    c->d_cc.release();
+    c->d_ck.release();
     for (Lane &ln : c->lanes) ln.release();
     if (c->side) cudaStreamDestroy(c->side);
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
@@ -562,6 +783,7 @@ void wally_destroy(wally_ctx *c)
         c->stage_ptrs[b].release();
     }
     c->tmp.release();
+    c->tmp32.release();
     delete c;
 }
 
@@ -591,6 +813,9 @@ int wally_query_info(const wally_ctx *c, wally_info *o)
     o->drop_c0 = c->drop0;
     o->drop_c1 = c->drop1;
     o->compressed_bytes = (uint64_t)(c->N / 8) * (c->bits0 + c->bits1);
+    o->store = c->num_clusters ? c->store : c->store_req;
+    o->cache_chunks = c->cache_chunks;
+    if (c->compact()) o->cluster_bytes = c->emb.n;
     return WALLY_OK;
 }
 
@@ -618,10 +843,23 @@ int wally_load_clusters(wally_ctx *c, uint32_t K, const uint32_t *sizes, const i
     // tile width: one tile of d_pad * ts words is 64 KB of shared memory
     uint32_t ts = std::max<uint32_t>(1, 8192 / c->d_pad);
     ts = std::min<uint32_t>(ts, 64);
-    const size_t words = (size_t)Z * c->L * c->N * c->d_pad;
+    const size_t words = (size_t)Z * c->chunk_words();
     c->ptxt.release();
+    c->emb.release();
+    c->row0.release();
+    c->csize.release();
+    c->d_cc.release();
+    c->d_ck.release();
     c->num_clusters = 0;
-    if (c->ptxt.ensure(words) != cudaSuccess)
+    uint32_t store = c->store_req;
+    if (store == WALLY_STORE_AUTO) {
+        size_t free_b = 0, total_b = 0;
+        CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        store = words * 8.0 <= 0.6 * (double)free_b ? WALLY_STORE_NTT : WALLY_STORE_COMPACT;
+    }
+    if (store == WALLY_STORE_COMPACT && c->cache_chunks < m_max)
+        return fail(WALLY_EINVAL, "cache_chunks = %u is below the largest cluster's %u chunks", c->cache_chunks, m_max);
+    if (store == WALLY_STORE_NTT && c->ptxt.ensure(words) != cudaSuccess)
         return fail(WALLY_ENOMEM, "cannot allocate %.1f GB for the encoded clusters", words * 8.0 / 1e9);
     std::vector<uint32_t> chunk_cluster(Z), chunk_k(Z);
     for (uint32_t i = 0; i < K; i++)
@@ -629,30 +867,32 @@ int wally_load_clusters(wally_ctx *c, uint32_t K, const uint32_t *sizes, const i
             chunk_cluster[chunk0[i] + k] = i;
             chunk_k[chunk0[i] + k] = k;
         }
-    int8_t *d_emb = nullptr;
-    u64 *d_row0 = nullptr;
-    u32 *d_size = nullptr, *d_cc = nullptr, *d_ck = nullptr;
-    CUDA_TRY(cudaMalloc(&d_emb, std::max<size_t>(1, rows * c->d)));
-    CUDA_TRY(cudaMalloc(&d_row0, 8 * std::max<size_t>(1, K)));
-    CUDA_TRY(cudaMalloc(&d_size, 4 * std::max<size_t>(1, K)));
-    CUDA_TRY(cudaMalloc(&d_cc, 4 * std::max<size_t>(1, Z)));
-    CUDA_TRY(cudaMalloc(&d_ck, 4 * std::max<size_t>(1, Z)));
-    if (rows) CUDA_TRY(cudaMemcpyAsync(d_emb, emb, rows * c->d, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(d_row0, row0.data(), 8 * (size_t)K, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(d_size, sizes, 4 * (size_t)K, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(d_cc, chunk_cluster.data(), 4 * (size_t)Z, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(d_ck, chunk_k.data(), 4 * (size_t)Z, cudaMemcpyHostToDevice, st));
-    for (uint64_t z0 = 0; z0 < Z; z0 += 65535) {
-        EncodeArgs a;
-        a.emb = d_emb;
-        a.row0 = d_row0;
-        a.size = d_size;
-        a.chunk_cluster = d_cc + z0;
-        a.chunk_k = d_ck + z0;
-        a.total_chunks = (uint32_t)std::min<uint64_t>(65535, Z - z0);
-        a.ptxt = c->ptxt.p + z0 * c->L * c->N * c->d_pad;
-        a.ts = ts;
-        CUDA_TRY(launch_encode_clusters(c->dp, a, st));
+    if (c->emb.ensure(std::max<size_t>(1, rows * c->d)) != cudaSuccess ||
+        c->row0.ensure(std::max<size_t>(1, K)) != cudaSuccess || c->csize.ensure(std::max<size_t>(1, K)) != cudaSuccess ||
+        c->d_cc.ensure(std::max<size_t>(1, Z)) != cudaSuccess || c->d_ck.ensure(std::max<size_t>(1, Z)) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate %.2f GB for the embeddings", rows * (double)c->d / 1e9);
+    if (rows) CUDA_TRY(cudaMemcpyAsync(c->emb.p, emb, rows * c->d, cudaMemcpyHostToDevice, st));
+    if (K) {
+        CUDA_TRY(cudaMemcpyAsync(c->row0.p, row0.data(), 8 * (size_t)K, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(c->csize.p, sizes, 4 * (size_t)K, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(c->d_cc.p, chunk_cluster.data(), 4 * (size_t)Z, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(c->d_ck.p, chunk_k.data(), 4 * (size_t)Z, cudaMemcpyHostToDevice, st));
+    }
+    c->ts = ts;
+    if (store == WALLY_STORE_NTT) {
+        for (uint64_t z0 = 0; z0 < Z; z0 += 65535) {
+            EncodeArgs a;
+            memset(&a, 0, sizeof(a));
+            a.emb = c->emb.p;
+            a.row0 = c->row0.p;
+            a.size = c->csize.p;
+            a.chunk_cluster = c->d_cc.p + z0;
+            a.chunk_k = c->d_ck.p + z0;
+            a.total_chunks = (uint32_t)std::min<uint64_t>(65535, Z - z0);
+            a.ptxt = c->ptxt.p + z0 * c->chunk_words();
+            a.ts = ts;
+            CUDA_TRY(launch_encode_clusters(c->dp, a, st));
+        }
     }
     if (c->d_chunks.ensure(std::max<uint32_t>(K, 1)) != cudaSuccess ||
         c->d_chunk0.ensure(std::max<uint32_t>(K, 1)) != cudaSuccess)
@@ -660,14 +900,22 @@ int wally_load_clusters(wally_ctx *c, uint32_t K, const uint32_t *sizes, const i
     CUDA_TRY(cudaMemcpyAsync(c->d_chunks.p, chunks.data(), 4 * (size_t)K, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(c->d_chunk0.p, chunk0.data(), 4 * (size_t)K, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(d_emb);
-    cudaFree(d_row0);
-    cudaFree(d_size);
-    cudaFree(d_cc);
-    cudaFree(d_ck);
+    if (store == WALLY_STORE_NTT) {
+        // the encoded store replaces the embeddings
+        c->emb.release();
+        c->row0.release();
+        c->csize.release();
+        c->d_cc.release();
+        c->d_ck.release();
+    }
+    for (Lane &ln : c->lanes) {
+        // a previous store's per-wave cache no longer matches
+        ln.cache.release();
+        ln.wchunk0.release();
+    }
+    c->store = store;
     c->num_clusters = K;
     c->m_max = m_max;
-    c->ts = ts;
     c->total_chunks = Z;
     c->h_chunks = chunks;
     c->h_chunk0 = chunk0;
@@ -687,7 +935,33 @@ int wally_export_cluster(wally_ctx *c, uint32_t id, uint64_t *out, void *stream)
     if (!c || !out) return fail(WALLY_EINVAL, "null argument");
     if (id >= c->num_clusters) return fail(WALLY_EINVAL, "cluster id %u out of range", id);
     DeviceGuard guard(c->device);
-    CUDA_TRY(launch_export_cluster(c->dp, cluster_store(c), id, c->h_chunks[id], out, (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->compact()) {
+        CUDA_TRY(launch_export_cluster(c->dp, cluster_store(c), id, c->h_chunks[id], out, st));
+        return WALLY_OK;
+    }
+    // compact store: encode the cluster's chunks into scratch, then export
+    const uint32_t m = c->h_chunks[id];
+    if (c->tmp.ensure((size_t)m * c->chunk_words()) != cudaSuccess || c->tmp32.ensure(c->num_clusters) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the export scratch");
+    EncodeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.emb = c->emb.p;
+    a.row0 = c->row0.p;
+    a.size = c->csize.p;
+    a.chunk_cluster = c->d_cc.p + c->h_chunk0[id];
+    a.chunk_k = c->d_ck.p + c->h_chunk0[id];
+    a.total_chunks = m;
+    a.ptxt = c->tmp.p;
+    a.ts = c->ts;
+    a.chunk0_out = c->tmp32.p;
+    CUDA_TRY(launch_encode_clusters(c->dp, a, st));
+    ClusterStore cs;
+    cs.ptxt = c->tmp.p;
+    cs.chunk0 = c->tmp32.p;
+    cs.chunks = c->d_chunks.p;
+    cs.ts = c->ts;
+    CUDA_TRY(launch_export_cluster(c->dp, cs, id, m, out, st));
     return WALLY_OK;
 }
 
@@ -702,25 +976,9 @@ int wally_eval_batch_lane(wally_ctx *c, uint32_t lane, uint32_t n, const uint32_
     if (!aligned16(cts) || !aligned16(keys) || !aligned16(out)) return fail(WALLY_EINVAL, "buffers must be 16-byte aligned");
     if (lane >= WALLY_MAX_LANES) return fail(WALLY_EINVAL, "lane %u out of range (%d lanes)", lane, WALLY_MAX_LANES);
     DeviceGuard guard(c->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    const uint32_t W = c->max_wave;
-    Lane &ln = c->lanes[lane];
-    int rc = ensure_workspace(c, ln, W, c->m_max);
-    if (rc) return rc;
-    const uint32_t K = c->num_clusters;
-    if (ln.counts.ensure(K) != cudaSuccess || ln.cstart.ensure(K + 1) != cudaSuccess ||
-        ln.fill.ensure(K) != cudaSuccess || ln.sorted_q.ensure(n) != cudaSuccess)
-        return fail(WALLY_ENOMEM, "cannot allocate the grouping arrays");
-    // a0: group by cluster
-    CUDA_TRY(launch_group(ids, n, K, ln.counts.p, ln.cstart.p, ln.fill.p, ln.sorted_q.p, c->d_err, st));
-    for (uint32_t wb = 0; wb < n; wb += W) {
-        const uint32_t len = std::min(W, n - wb);
-        CUDA_TRY(launch_gather_wave(ln.wp, ln.sorted_q.p, ids, ln.cstart.p, K, wb, len, cts, keys, input_index,
-                                    out_offsets, out, c->ctw(), c->keysw(), st));
-        rc = run_wave(c, ln, ln.wp, len, st);
-        if (rc) return rc;
-    }
-    return WALLY_OK;
+    Lane *ls[1] = {&c->lanes[lane]};
+    cudaStream_t ss[1] = {(cudaStream_t)stream};
+    return eval_device(c, ls, ss, 1, n, ids, cts, keys, input_index, out_offsets, out);
 }
 
 // Waves alternate between lane 0 on the caller's stream and lane 1 on the
@@ -731,42 +989,21 @@ int wally_eval_batch(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64
                      const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out, void *stream)
 {
     if (!c) return fail(WALLY_EINVAL, "null context");
-    if (n <= c->max_wave) return wally_eval_batch_lane(c, 0, n, ids, cts, keys, input_index, out_offsets, out, stream);
+    if (n <= c->max_wave && !c->compact())
+        return wally_eval_batch_lane(c, 0, n, ids, cts, keys, input_index, out_offsets, out, stream);
     if (!c->num_clusters) return fail(WALLY_ESTATE, "no clusters loaded");
+    if (n == 0) return WALLY_OK;
     if (!ids || !cts || !keys || !out_offsets || !out) return fail(WALLY_EINVAL, "null argument");
     if (!aligned16(cts) || !aligned16(keys) || !aligned16(out)) return fail(WALLY_EINVAL, "buffers must be 16-byte aligned");
     DeviceGuard guard(c->device);
-    cudaStream_t st = (cudaStream_t)stream;
     if (!c->side) {
         CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
         CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
     }
-    const uint32_t W = c->max_wave, K = c->num_clusters;
-    Lane &l0 = c->lanes[0], &l1 = c->lanes[1];
-    int rc = ensure_workspace(c, l0, W, c->m_max);
-    if (rc == WALLY_OK) rc = ensure_workspace(c, l1, W, c->m_max);
-    if (rc) return rc;
-    if (l0.counts.ensure(K) != cudaSuccess || l0.cstart.ensure(K + 1) != cudaSuccess ||
-        l0.fill.ensure(K) != cudaSuccess || l0.sorted_q.ensure(n) != cudaSuccess)
-        return fail(WALLY_ENOMEM, "cannot allocate the grouping arrays");
-    // a0: group by cluster (shared by both lanes)
-    CUDA_TRY(launch_group(ids, n, K, l0.counts.p, l0.cstart.p, l0.fill.p, l0.sorted_q.p, c->d_err, st));
-    CUDA_TRY(cudaEventRecord(c->fork_ev, st));
-    CUDA_TRY(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
-    uint32_t w = 0;
-    for (uint32_t wb = 0; wb < n; wb += W, w++) {
-        const uint32_t len = std::min(W, n - wb);
-        Lane &ln = (w & 1) ? l1 : l0;
-        cudaStream_t s = (w & 1) ? c->side : st;
-        CUDA_TRY(launch_gather_wave(ln.wp, l0.sorted_q.p, ids, l0.cstart.p, K, wb, len, cts, keys, input_index,
-                                    out_offsets, out, c->ctw(), c->keysw(), s));
-        rc = run_wave(c, ln, ln.wp, len, s);
-        if (rc) return rc;
-    }
-    CUDA_TRY(cudaEventRecord(c->join_ev, c->side));
-    CUDA_TRY(cudaStreamWaitEvent(st, c->join_ev, 0));
-    return WALLY_OK;
+    Lane *ls[2] = {&c->lanes[0], &c->lanes[1]};
+    cudaStream_t ss[2] = {(cudaStream_t)stream, c->side};
+    return eval_device(c, ls, ss, 2, n, ids, cts, keys, input_index, out_offsets, out);
 }
 
 int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
@@ -783,6 +1020,7 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
         if (ids[q] >= K) return fail(WALLY_EINVAL, "query %u names cluster %u of %u", q, ids[q], K);
     Lane &ln = c->lanes[0];
     int rc = ensure_workspace(c, ln, W, c->m_max);
+    if (rc == WALLY_OK && c->compact()) rc = ensure_cache(c, ln);
     if (rc) return rc;
     const size_t ctw = c->ctw(), keysw = c->keysw();
     for (int b = 0; b < 2; b++) {
@@ -799,6 +1037,17 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
     {
         std::vector<uint32_t> fillh(start.begin(), start.end() - 1);
         for (uint32_t q = 0; q < n; q++) order[fillh[ids[q]]++] = q;
+    }
+    std::vector<Wave> waves;
+    std::vector<uint32_t> zc, zk;
+    if (c->compact()) {
+        std::vector<uint32_t> cnt(K);
+        for (uint32_t k = 0; k < K; k++) cnt[k] = start[k + 1] - start[k];
+        compact_waves(c, cnt.data(), W, waves, zc, zk);
+        rc = upload_chunk_list(ln, zc, zk, st);
+        if (rc) return rc;
+    } else {
+        fixed_waves(n, W, waves);
     }
     cudaStream_t cin = nullptr, cout_ = nullptr;
     CUDA_TRY(cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking));
@@ -819,11 +1068,10 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
         CUDA_TRY(cudaMallocHost(&h_planptr[b], sizeof(void *) * 3 * (size_t)W));
     }
     std::vector<uint32_t> pair_off(W + 1);
-    int wave = 0;
     rc = WALLY_OK;
-    for (uint32_t wb = 0; wb < n && rc == WALLY_OK; wb += W, wave++) {
+    for (size_t wave = 0; wave < waves.size() && rc == WALLY_OK; wave++) {
         const int b = wave & 1;
-        const uint32_t len = std::min(W, n - wb);
+        const uint32_t wb = waves[wave].begin, len = waves[wave].len;
         // buffer b is free once the compute and the read-back of wave - 2 are done
         if (cudaEventSynchronize(comp_done[b]) != cudaSuccess) { rc = fail(WALLY_ECUDA, "event sync"); break; }
         uint32_t *p32 = h_plan32[b];
@@ -859,7 +1107,8 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
         CUDA_TRY(cudaEventRecord(in_done[b], cin));
         CUDA_TRY(cudaStreamWaitEvent(st, in_done[b], 0));
         CUDA_TRY(cudaStreamWaitEvent(st, out_done[b], 0));
-        rc = run_wave(c, ln, wp, len, st);
+        if (c->compact()) rc = encode_wave(c, ln, waves[wave], ln.zlist.p, zc.size(), st);
+        if (rc == WALLY_OK) rc = run_wave(c, ln, wp, len, wave_store(c, ln), st);
         if (rc) break;
         CUDA_TRY(cudaEventRecord(comp_done[b], st));
         CUDA_TRY(cudaStreamWaitEvent(cout_, comp_done[b], 0));
@@ -950,7 +1199,7 @@ int wally_profile_enable(wally_ctx *c, int enable)
 
 int wally_profile_read(wally_ctx *c, wally_kernel_time *out, uint32_t cap, uint32_t *count)
 {
-    static const char *names[KK_COUNT] = {"to_ntt", "ks_a", "ks_b", "ks_c", "mac", "output", "plan"};
+    static const char *names[KK_COUNT] = {"to_ntt", "ks_a", "ks_b", "ks_c", "mac", "output", "plan", "encode"};
     if (!c || !count) return fail(WALLY_EINVAL, "null argument");
     DeviceGuard guard(c->device);
     CUDA_TRY(cudaDeviceSynchronize());

@@ -61,7 +61,7 @@ struct ClusterStore {
 };
 
 // Optional timing of every launch with CUDA events on the launch stream.
-enum KernelKind { KK_TO_NTT = 0, KK_KS_A, KK_KS_B, KK_KS_C, KK_MAC, KK_OUTPUT, KK_PLAN, KK_COUNT };
+enum KernelKind { KK_TO_NTT = 0, KK_KS_A, KK_KS_B, KK_KS_C, KK_MAC, KK_OUTPUT, KK_PLAN, KK_ENCODE, KK_COUNT };
 struct Profiler {
     virtual void begin(int kind, cudaStream_t st) = 0;
     virtual void end(int kind, cudaStream_t st) = 0;
@@ -103,8 +103,9 @@ struct EncodeArgs {
     u32 total_chunks;
     u64 *ptxt;
     u32 ts;
+    u32 *chunk0_out;     // optional [K]: chunk0_out[c] = local index of chunk (c, 0)
 };
-cudaError_t launch_encode_clusters(const DevParams &dp, const EncodeArgs &a, cudaStream_t st);
+cudaError_t launch_encode_clusters(const DevParams &dp, const EncodeArgs &a, cudaStream_t st, Profiler *pr = nullptr);
 cudaError_t launch_export_cluster(const DevParams &dp, const ClusterStore &cs, u32 cluster, u32 m, u64 *out,
                                   cudaStream_t st);
 

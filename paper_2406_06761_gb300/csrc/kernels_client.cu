@@ -1,8 +1,9 @@
 // kernels_client.cu -- set-up and client-side kernels of the Wally GB300
 // library: cluster encoding (Alg. "Server Initialization"), its export back to
 // coefficient form, and the client operations of Sec. 2 / Alg. "Client Query
-// Generation" (query encoding, encryption, Galois keys, decryption).  None of
-// these is on the timed server path.
+// Generation" (query encoding, encryption, Galois keys, decryption).  Only the
+// cluster encoding also runs on the server path, when the compact cluster
+// store encodes each wave's chunks on the fly.
 #include "kernels.hpp"
 
 namespace wally {
@@ -48,6 +49,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_encode_cluster(const DevParams *dpp, EncodeA
     const u32 i = ib / g, b = ib % g, j = g * i + b, shift = (g * i) % HALF;
     const u32 c = a.chunk_cluster[z], k = a.chunk_k[z], size = a.size[c];
     const u64 row0 = a.row0[c];
+    if (a.chunk0_out && ib == 0 && k == 0 && threadIdx.x == 0) a.chunk0_out[c] = z;
     load_mod(&md, dpp, L + 1);
     const u64 t = md.p;
 #pragma unroll 4
@@ -502,13 +504,21 @@ cudaError_t set_client_kernel_attributes(int log_n)
     return e;
 }
 
-cudaError_t launch_encode_clusters(const DevParams &dp, const EncodeArgs &a, cudaStream_t st)
+static cudaError_t encode_dispatch(const DevParams *dpp, int log_n, dim3 grid, const EncodeArgs &a, cudaStream_t st)
+{
+    DISPATCH_LOGN(log_n, (k_encode_cluster<LG><<<grid, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_clusters(const DevParams &dp, const EncodeArgs &a, cudaStream_t st, Profiler *pr)
 {
     if (a.total_chunks == 0) return cudaSuccess;
     const DevParams *dpp = device_params_of(dp);
     dim3 grid(dp.g * dp.h, a.total_chunks);
-    DISPATCH_LOGN(dp.log_n, (k_encode_cluster<LG><<<grid, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, a)));
-    return cudaGetLastError();
+    if (pr) pr->begin(KK_ENCODE, st);
+    cudaError_t e = encode_dispatch(dpp, dp.log_n, grid, a, st);
+    if (pr) pr->end(KK_ENCODE, st);
+    return e;
 }
 
 cudaError_t launch_export_cluster(const DevParams &dp, const ClusterStore &cs, u32 cluster, u32 m, u64 *out,

@@ -34,14 +34,14 @@ class Pool:
 class DeviceWorkload:
     def __init__(self, name: str, seed: int = 0, device: int = 0, pool: int | None = None, max_wave: int = 0,
                  real_queries: int | None = None, num_clusters: int | None = None, sizes=None,
-                 keep_embeddings: bool = True, verbose: bool = False):
+                 keep_embeddings: bool = True, verbose: bool = False, **ctx_kw):
         w = W.WORKLOADS[name]
         if real_queries is not None or num_clusters is not None:
             w = dataclasses.replace(w, real_queries=real_queries if real_queries is not None else w.real_queries,
                                     num_clusters=num_clusters if num_clusters is not None else w.num_clusters)
         self.w, self.seed, self.verbose = w, seed, verbose
         self.dev = torch.device("cuda", device)
-        self.ctx = Wl.Context(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim, device=device, max_wave=max_wave)
+        self.ctx = Wl.Context(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim, device=device, max_wave=max_wave, **ctx_kw)
         info = self.ctx.info
         self.N, self.L, self.q, self.P = info.n, info.num_q, self.ctx.q, self.ctx.P
         self.ctw, self.keysw = int(info.ct_words), int(info.keys_words)

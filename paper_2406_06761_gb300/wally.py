@@ -17,6 +17,7 @@ from . import build as _build
 
 WALLY_OK, WALLY_EINVAL, WALLY_ENOMEM, WALLY_ECUDA, WALLY_ETIMEOUT, WALLY_ESTATE = range(6)
 MAX_LIMBS = 8
+STORE_AUTO, STORE_NTT, STORE_COMPACT = 0, 1, 2
 
 
 class WallyError(RuntimeError):
@@ -30,7 +31,7 @@ class wally_params(ctypes.Structure):
         ("log_n", ctypes.c_uint32), ("num_q", ctypes.c_uint32), ("q_bits", ctypes.c_uint32),
         ("t_bits", ctypes.c_uint32), ("dim", ctypes.c_uint32), ("device", ctypes.c_int32),
         ("q", ctypes.POINTER(ctypes.c_uint64)), ("p_special", ctypes.c_uint64), ("t", ctypes.c_uint64),
-        ("max_wave", ctypes.c_uint32),
+        ("max_wave", ctypes.c_uint32), ("store", ctypes.c_uint32), ("cache_chunks", ctypes.c_uint32),
     ]
 
 
@@ -43,7 +44,7 @@ class wally_info(ctypes.Structure):
         ("k1", ctypes.c_uint64), ("kg", ctypes.c_uint64), ("ct_words", ctypes.c_uint64),
         ("keys_words", ctypes.c_uint64), ("total_chunks", ctypes.c_uint64), ("cluster_bytes", ctypes.c_uint64),
         ("max_wave", ctypes.c_uint32), ("drop_c0", ctypes.c_uint32), ("drop_c1", ctypes.c_uint32),
-        ("compressed_bytes", ctypes.c_uint64),
+        ("compressed_bytes", ctypes.c_uint64), ("store", ctypes.c_uint32), ("cache_chunks", ctypes.c_uint32),
     ]
 
 
@@ -139,9 +140,10 @@ def _u64_view(t: torch.Tensor) -> torch.Tensor:
 # ------------------------------------------------------------------ same names as the C ABI
 
 def wally_setup_params(log_n: int, num_q: int, q_bits: int, t_bits: int, dim: int, device: int = 0,
-                       q=None, p_special: int = 0, t: int = 0, max_wave: int = 0) -> int:
+                       q=None, p_special: int = 0, t: int = 0, max_wave: int = 0, store: int = STORE_AUTO,
+                       cache_chunks: int = 0) -> int:
     lib = load()
-    prm = wally_params(log_n, num_q, q_bits, t_bits, dim, device, None, p_special, t, max_wave)
+    prm = wally_params(log_n, num_q, q_bits, t_bits, dim, device, None, p_special, t, max_wave, store, cache_chunks)
     qarr = None
     if q is not None:
         qarr = (ctypes.c_uint64 * len(q))(*q)

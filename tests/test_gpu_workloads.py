@@ -112,20 +112,18 @@ def test_wide_workload_sampled():
     ctx.close()
 
 
-def test_full_scale_batch_sampled():
-    """The full-scale batch as bench.py runs it: 3.2M x 192 in 1,800 clusters,
-    500,000 real queries + fakes, a 2,048-client pool, waves of 1,024, the
-    batch split into calls whose outputs share one buffer.  Sampled outputs
-    are checked bit for bit against the oracle, and a larger sample by GPU
-    decryption against the plain dot products."""
-    wl = H.DeviceWorkload("full_scale", pool=2048, max_wave=1024)
-    prm = O.params(wl.w.log_n, wl.w.num_q, wl.w.q_bits, wl.w.t_bits, wl.w.dim)
+def _whole_batch_sampled(wl, prm, n_exact, n_decrypt, seed, ends=True):
+    """Evaluate every query of the workload's batch (split into calls whose
+    outputs share one buffer); keep sampled outputs, check them by GPU
+    decryption against the plain dot products and a few bit for bit against
+    the oracle (with ends: also the first and last query and the first fake)."""
     free, _ = torch.cuda.mem_get_info(wl.dev)
     subs = wl.sub_batches(int(free * 0.5))
-    rng = np.random.default_rng(7)
-    exact = set(rng.choice(wl.n, size=4, replace=False).tolist()) | {0, wl.n - 1}
-    exact.add(int(np.flatnonzero(~wl.is_real)[0]))
-    decrypt = set(rng.choice(wl.n, size=256, replace=False).tolist())
+    rng = np.random.default_rng(seed)
+    exact = set(rng.choice(wl.n, size=n_exact, replace=False).tolist())
+    if ends:
+        exact |= {0, wl.n - 1, int(np.flatnonzero(~wl.is_real)[0])}
+    decrypt = set(rng.choice(wl.n, size=n_decrypt, replace=False).tolist())
     keep = {}
     out = None
     for lo, hi in subs:
@@ -140,6 +138,7 @@ def test_full_scale_batch_sampled():
                 m = int(wl.chunks[wl.ids[qi]])
                 keep[qi] = out[int(offs[qi - lo]):int(offs[qi - lo]) + m].clone()
     assert len(subs) >= 1 and len(keep) == len(exact | decrypt)
+    del out
     secrets = wl.secrets()
     for qi in sorted(decrypt | exact):
         ct = keep[qi]
@@ -152,6 +151,32 @@ def test_full_scale_batch_sampled():
         assert np.array_equal(sc[:len(expect)], expect) and np.all(sc[len(expect):] == 0), qi
     for qi in sorted(exact):
         _oracle_check(wl, prm, qi, Wl.to_u64_numpy(keep[qi]))
+
+
+def test_full_scale_batch_sampled():
+    """The full-scale batch as bench.py runs it: 3.2M x 192 in 1,800 clusters,
+    500,000 real queries + fakes, a 2,048-client pool, waves of 1,024, the
+    batch split into calls whose outputs share one buffer.  Sampled outputs
+    are checked bit for bit against the oracle, and a larger sample by GPU
+    decryption against the plain dot products."""
+    wl = H.DeviceWorkload("full_scale", pool=2048, max_wave=1024)
+    prm = O.params(wl.w.log_n, wl.w.num_q, wl.w.q_bits, wl.w.t_bits, wl.w.dim)
+    _whole_batch_sampled(wl, prm, 4, 256, seed=7)
+    wl.close()
+
+
+def test_wide_full_size_sampled():
+    """The wide workload at its full size: 1M x 768 (entries in [-7, 7]) in
+    1,000 log-normal clusters, N = 16384, six 50-bit limbs, 100,000 real
+    queries + fakes.  Its encoded clusters (805 MB a chunk) do not fit in
+    device memory, so the store is the compact one (chosen automatically):
+    every wave encodes its chunks on the fly.  Pool of 256 clients, waves of
+    128 as bench.py --workload wide runs it."""
+    wl = H.DeviceWorkload("wide", pool=256, max_wave=128)
+    assert wl.ctx.info.store == Wl.STORE_COMPACT
+    assert int(wl.sizes.sum()) == 1_000_000 and len(wl.sizes) == 1000
+    prm = O.params(wl.w.log_n, wl.w.num_q, wl.w.q_bits, wl.w.t_bits, wl.w.dim)
+    _whole_batch_sampled(wl, prm, 1, 64, seed=8, ends=False)
     wl.close()
 
 

@@ -209,6 +209,33 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 
+def autotune(wl, Wl):
+    """Pick the launch shapes (wave size, lanes, MAC and transform CTAs per
+    SM) with the library's autotuner (staged search) on a sample of the
+    batch, before any timing.  N = 16384 uses a smaller grid and sample (a
+    wave workspace of 130 MB a query)."""
+    import torch
+    t0 = time.perf_counter()
+    if wl.ctx.info.log_n >= 14:
+        cands = [dict(max_wave=w, lanes=l, mac_ctas_per_sm=3, ntt_ctas_per_sm=0) for w in (64, 128, 256) for l in (1, 2)]
+        sample = 512
+    else:
+        cands, sample = None, 16384  # four waves a lane of the largest wave size
+    b = wl.device_batch(0, min(wl.n, sample))
+    out = wl.alloc_out(b[3])
+    best, table = Wl.wally_autotune(wl.ctx.ptr, b[0].numel(), b[0], wl.pool.cts, wl.pool.keys, b[1], b[2], out,
+                                    candidates=cands, reps=2)
+    del out
+    torch.cuda.empty_cache()
+    ranked = sorted((t for t in table if t[1] > 0), key=lambda t: t[1])
+    res = {"chosen": table[best][0], "sample_queries": int(b[0].numel()), "candidates": len(table),
+           "skipped_out_of_memory": sum(1 for t in table if t[1] < 0), "seconds": time.perf_counter() - t0,
+           "fastest": [{"shape": sh, "us_per_query": ms * 1e3} for sh, ms in ranked[:5]],
+           "slowest": {"shape": ranked[-1][0], "us_per_query": ranked[-1][1] * 1e3} if ranked else None}
+    log("autotune", res)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,7 +244,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="full_scale")
     ap.add_argument("--pool", type=int, default=2048)
-    ap.add_argument("--max-wave", type=int, default=0)
+    ap.add_argument("--max-wave", type=int, default=0, help="fixed wave size (no autotuning)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shapes")
+    ap.add_argument("--shape", default=None, help="fixed launch shape max_wave,lanes,mac_ctas,ntt_ctas (no autotuning)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -252,6 +281,14 @@ def main():
     t_setup = time.perf_counter()
     wl = H.DeviceWorkload(args.workload, device=local, pool=args.pool, max_wave=args.max_wave,
                           real_queries=args.real_queries, keep_embeddings=False, verbose=(rank == 0))
+    tuning = None
+    if args.shape:
+        w_, l_, m_, k_ = (int(v) for v in args.shape.split(","))
+        Wl.wally_set_tuning(wl.ctx.ptr, w_, l_, m_, k_)
+        tuning = {"chosen": Wl.wally_get_tuning(wl.ctx.ptr).as_dict(), "fixed": True}
+    elif not args.max_wave and not args.no_autotune:
+        tuning = autotune(wl, Wl)
+    wl.ctx.refresh()
     info = wl.ctx.info
     n = wl.n
     n_real = int(wl.is_real.sum())
@@ -400,6 +437,7 @@ def main():
         "clocks": clk,
         "e2e": e2e,
         "one_query_path": single,
+        "tuning": tuning,
         "cpu_baseline": cpu,
     }
     if rank == 0:

@@ -261,6 +261,59 @@ int wally_profile_read(wally_ctx *ctx, wally_kernel_time *out, uint32_t cap, uin
  * roofline.  Synchronous; allocates a few kilobytes. */
 int wally_measure_int_peaks(int32_t device, double *modmul_per_s, double *butterfly_per_s, double *mac128_per_s);
 
+/* ---------------------------------------------------------------- launch shapes
+ * The paper has no counterpart: these choose how the batch is laid onto this
+ * GPU, never what is computed (every shape gives the same bits).
+ *   max_wave         queries per wave (the wave workspace grows with it:
+ *                    about 25 MB a query at N = 8192, L = 3)
+ *   lanes            1: the waves of a wally_eval_batch call run in sequence
+ *                    on the caller's stream; 2: they alternate between two
+ *                    streams (lanes 0 and 1) so that one wave's kernels fill
+ *                    the other's idle SMs
+ *   mac_ctas_per_sm  1..3: resident CTAs per SM of the persistent
+ *                    multiply-accumulate kernel (its grid)
+ *   ntt_ctas_per_sm  0: as many transform-kernel CTAs per SM as shared memory
+ *                    allows; k > 0: at most k (they are launched with more
+ *                    shared memory than they use)
+ * Defaults: 1024 (or the max_wave of wally_params), 2, 3, 0. */
+typedef struct {
+    uint32_t max_wave;
+    uint32_t lanes;
+    uint32_t mac_ctas_per_sm;
+    uint32_t ntt_ctas_per_sm;
+} wally_tuning;
+
+int wally_get_tuning(const wally_ctx *ctx, wally_tuning *out);
+
+/* Errors: WALLY_EINVAL (max_wave 0, lanes not 1 or 2, mac_ctas_per_sm not
+ * 1..3).  An ntt_ctas_per_sm at or above what shared memory allows anyway is
+ * no cap.  Takes effect at the next call; it must not overlap running
+ * evaluations of the context. */
+int wally_set_tuning(wally_ctx *ctx, const wally_tuning *tuning);
+
+/* Autotuner: evaluates the sample batch (the arguments of wally_eval_batch,
+ * device buffers; `out` is overwritten) once untimed and `reps` times timed
+ * with CUDA events on `stream` under each candidate shape, keeps the fastest
+ * in the context and returns its index in *best.  With candidates non-NULL
+ * the candidates are candidates[0 .. num_candidates).  With candidates NULL
+ * (num_candidates 0) the search is staged: max_wave in {512, 1024, 2048} x
+ * lanes in {1, 2} with mac 3, ntt 0; then, at the best of those,
+ * mac_ctas_per_sm in {2, 3} x ntt_ctas_per_sm in {0, 2} (9 shapes in all).
+ * tried (host, [WALLY_AUTOTUNE_MAX] or [num_candidates], may be NULL)
+ * receives the shapes in the order timed, ms_per_query (same length, may be
+ * NULL) their mean device milliseconds per query of the sample, or -1 where
+ * the shape's workspace did not fit in device memory (skipped), and
+ * *num_tried (may be NULL) their number.  Synchronous; frees the wave
+ * workspaces between shapes.  For the timings to stand for a large batch,
+ * the sample should hold several waves per lane of the largest max_wave.
+ * Errors: WALLY_EINVAL, WALLY_ESTATE (no clusters), WALLY_ENOMEM (no shape
+ * fits), WALLY_ECUDA. */
+#define WALLY_AUTOTUNE_MAX 16
+int wally_autotune(wally_ctx *ctx, const wally_tuning *candidates, uint32_t num_candidates, uint32_t reps,
+                   uint32_t n, const uint32_t *cluster_ids, const uint64_t *cts, const uint64_t *galois_keys,
+                   const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out,
+                   wally_tuning *tried, double *ms_per_query, uint32_t *num_tried, uint32_t *best, void *stream);
+
 /* ---------------------------------------------------------------- client side
  * Sec. 2 and Alg. "Client Query Generation".  The random numbers a client
  * draws are inputs, so that results are reproducible:

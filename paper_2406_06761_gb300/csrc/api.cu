@@ -64,7 +64,10 @@ struct DevBuf {
         n = 0;
         cudaError_t e = cudaMalloc((void **)&p, sizeof(T) * (count ? count : 1));
         if (e == cudaSuccess) n = count;
-        else p = nullptr;
+        else {
+            p = nullptr;
+            cudaGetLastError();  // a failed allocation must not surface at the next launch check
+        }
         return e;
     }
     void release()
@@ -88,7 +91,10 @@ struct PinnedBuf {
         n = 0;
         cudaError_t e = cudaMallocHost((void **)&p, sizeof(T) * (count ? count : 1));
         if (e == cudaSuccess) n = count;
-        else p = nullptr;
+        else {
+            p = nullptr;
+            cudaGetLastError();
+        }
         return e;
     }
     void release()
@@ -195,6 +201,8 @@ struct wally_ctx {
     uint32_t drop0 = 0, drop1 = 0, bits0 = 0, bits1 = 0;  // response compression
     uint32_t max_wave = 1024;
     uint32_t store_req = WALLY_STORE_AUTO, store = WALLY_STORE_NTT, cache_chunks = 16;
+    uint32_t lanes_pref = 2, ntt_cps = 0;  // launch shapes (wally_tuning)
+    int smem_per_sm = 0, smem_reserved = 0;
     DevParams dp{};
     DevParams *d_dp = nullptr;
     std::vector<void *> tables;
@@ -636,6 +644,58 @@ int eval_device(wally_ctx *c, Lane *const *lanes, const cudaStream_t *streams, i
     return WALLY_OK;
 }
 
+// ---------------------------------------------------------------- launch shapes
+// Dynamic shared memory that holds the transform kernels to at most k CTAs
+// per SM (0: what they need).
+uint32_t ntt_smem_for(const wally_ctx *c, uint32_t k)
+{
+    const uint32_t need = (uint32_t)ntt_smem_need(c->log_n);
+    if (!k || c->smem_per_sm <= 0) return 0;
+    const int per = c->smem_per_sm / (int)(k + 1) - c->smem_reserved;  // k + 1 CTAs must not fit
+    uint32_t dyn = per > 0 ? ((uint32_t)per + 15u) & ~15u : 0;
+    if (dyn <= need) return 0;  // the need alone already limits the CTAs
+    if (dyn > 226u * 1024u) return 0;  // the most the transform kernels are set up to take
+    return dyn;
+}
+
+int apply_tuning(wally_ctx *c, const wally_tuning *t)
+{
+    if (!t->max_wave) return fail(WALLY_EINVAL, "max_wave must be positive");
+    if (t->lanes != 1 && t->lanes != 2) return fail(WALLY_EINVAL, "lanes must be 1 or 2");
+    if (t->mac_ctas_per_sm < 1 || t->mac_ctas_per_sm > 3) return fail(WALLY_EINVAL, "mac_ctas_per_sm must be 1..3");
+    c->max_wave = t->max_wave;
+    c->lanes_pref = t->lanes;
+    c->dp.mac_ctas_per_sm = t->mac_ctas_per_sm;
+    c->ntt_cps = t->ntt_ctas_per_sm;
+    c->dp.ntt_smem = ntt_smem_for(c, t->ntt_ctas_per_sm);
+    return WALLY_OK;
+}
+
+void current_tuning(const wally_ctx *c, wally_tuning *t)
+{
+    t->max_wave = c->max_wave;
+    t->lanes = c->lanes_pref;
+    t->mac_ctas_per_sm = c->dp.mac_ctas_per_sm ? c->dp.mac_ctas_per_sm : 3;
+    t->ntt_ctas_per_sm = c->ntt_cps;
+}
+
+void release_waves(wally_ctx *c)
+{
+    for (Lane &ln : c->lanes) {
+        ln.keysN.release();
+        ln.ctp.release();
+        ln.T.release();
+        ln.S.release();
+        ln.sc.release();
+        ln.dg.release();
+        ln.u.release();
+        ln.dd.release();
+        ln.plan_u32.release();
+        ln.plan_ptr.release();
+        ln.ws_wave = ln.ws_mmax = 0;
+    }
+}
+
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
@@ -744,6 +804,8 @@ int wally_setup_params(const wally_params *prm, wally_ctx **out)
         c->bits1 = bits(c->drop1);
     }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
+    cudaDeviceGetAttribute(&c->smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, c->device);
     int rc = setup_tables(c);
     if (rc != WALLY_OK) {
         std::string msg = g_err;
@@ -989,7 +1051,7 @@ int wally_eval_batch(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64
                      const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out, void *stream)
 {
     if (!c) return fail(WALLY_EINVAL, "null context");
-    if (n <= c->max_wave && !c->compact())
+    if ((n <= c->max_wave || c->lanes_pref == 1) && !c->compact())
         return wally_eval_batch_lane(c, 0, n, ids, cts, keys, input_index, out_offsets, out, stream);
     if (!c->num_clusters) return fail(WALLY_ESTATE, "no clusters loaded");
     if (n == 0) return WALLY_OK;
@@ -1003,7 +1065,7 @@ int wally_eval_batch(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64
     }
     Lane *ls[2] = {&c->lanes[0], &c->lanes[1]};
     cudaStream_t ss[2] = {(cudaStream_t)stream, c->side};
-    return eval_device(c, ls, ss, 2, n, ids, cts, keys, input_index, out_offsets, out);
+    return eval_device(c, ls, ss, (int)c->lanes_pref, n, ids, cts, keys, input_index, out_offsets, out);
 }
 
 int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
@@ -1171,6 +1233,116 @@ int wally_rotate(wally_ctx *c, uint32_t n, uint64_t k, const uint64_t *cts, cons
         CUDA_TRY(launch_from_ntt(c->dp, ln.S.p, out + (size_t)x0 * ctw, 2 * c->L, c->L, cnt, st));
     }
     return WALLY_OK;
+}
+
+int wally_get_tuning(const wally_ctx *c, wally_tuning *out)
+{
+    if (!c || !out) return fail(WALLY_EINVAL, "null argument");
+    current_tuning(c, out);
+    return WALLY_OK;
+}
+
+int wally_set_tuning(wally_ctx *c, const wally_tuning *t)
+{
+    if (!c || !t) return fail(WALLY_EINVAL, "null argument");
+    return apply_tuning(c, t);
+}
+
+// Mean device milliseconds per query of the sample under shape t (one
+// untimed call, then reps timed ones), or -1 if its workspace does not fit.
+int time_shape(wally_ctx *c, const wally_tuning &t, uint32_t reps, uint32_t n, const uint32_t *ids,
+               const uint64_t *cts, const uint64_t *keys, const uint32_t *input_index, const uint64_t *out_offsets,
+               uint64_t *out, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, double *ms_out)
+{
+    release_waves(c);
+    int rc = apply_tuning(c, &t);
+    if (rc) return rc;
+    rc = wally_eval_batch(c, n, ids, cts, keys, input_index, out_offsets, out, st);
+    if (rc == WALLY_ENOMEM) {
+        *ms_out = -1;
+        return WALLY_OK;
+    }
+    if (rc) return rc;
+    CUDA_TRY(cudaEventRecord(e0, st));
+    for (uint32_t k = 0; k < reps; k++) {
+        rc = wally_eval_batch(c, n, ids, cts, keys, input_index, out_offsets, out, st);
+        if (rc) return rc;
+    }
+    CUDA_TRY(cudaEventRecord(e1, st));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *ms_out = (double)ms / reps / n;
+    return WALLY_OK;
+}
+
+int wally_autotune(wally_ctx *c, const wally_tuning *cand, uint32_t nc, uint32_t reps, uint32_t n, const uint32_t *ids,
+                   const uint64_t *cts, const uint64_t *keys, const uint32_t *input_index, const uint64_t *out_offsets,
+                   uint64_t *out, wally_tuning *tried, double *ms_per_query, uint32_t *num_tried, uint32_t *best,
+                   void *stream)
+{
+    if (!c || !best) return fail(WALLY_EINVAL, "null argument");
+    if (!c->num_clusters) return fail(WALLY_ESTATE, "no clusters loaded");
+    if (!n) return fail(WALLY_EINVAL, "empty sample");
+    if (!cand && nc) return fail(WALLY_EINVAL, "num_candidates must be 0 without candidates");
+    if (cand && !nc) return fail(WALLY_EINVAL, "no candidates");
+    for (uint32_t i = 0; cand && i < nc; i++)
+        if (!cand[i].max_wave || (cand[i].lanes != 1 && cand[i].lanes != 2) || cand[i].mac_ctas_per_sm < 1 ||
+            cand[i].mac_ctas_per_sm > 3)
+            return fail(WALLY_EINVAL, "invalid candidate shape %u", i);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    wally_tuning keep;
+    current_tuning(c, &keep);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    reps = std::max(reps, 1u);
+    std::vector<wally_tuning> done;
+    std::vector<double> ms;
+    int rc = WALLY_OK;
+    auto run = [&](const wally_tuning &t) {
+        double m = -1;
+        if (rc == WALLY_OK) rc = time_shape(c, t, reps, n, ids, cts, keys, input_index, out_offsets, out, st, e0, e1, &m);
+        done.push_back(t);
+        ms.push_back(m);
+    };
+    auto best_of = [&]() {
+        int bi = -1;
+        for (size_t i = 0; i < ms.size(); i++)
+            if (ms[i] > 0 && (bi < 0 || ms[i] < ms[bi])) bi = (int)i;
+        return bi;
+    };
+    if (cand) {
+        for (uint32_t i = 0; i < nc && rc == WALLY_OK; i++) run(cand[i]);
+    } else {
+        for (uint32_t w : {512u, 1024u, 2048u})
+            for (uint32_t l : {1u, 2u}) run(wally_tuning{w, l, 3, 0});
+        const int b1 = best_of();
+        if (rc == WALLY_OK && b1 >= 0) {
+            const wally_tuning base = done[b1];
+            for (uint32_t m : {2u, 3u})
+                for (uint32_t k : {0u, 2u})
+                    if (!(m == 3 && k == 0)) run(wally_tuning{base.max_wave, base.lanes, m, k});
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release_waves(c);
+    const int bi = best_of();
+    if (rc == WALLY_OK && bi < 0) rc = fail(WALLY_ENOMEM, "no candidate shape fits in device memory");
+    if (rc) {
+        apply_tuning(c, &keep);
+        return rc;
+    }
+    const size_t cap = cand ? nc : WALLY_AUTOTUNE_MAX;
+    for (size_t i = 0; i < done.size() && i < cap; i++) {
+        if (tried) tried[i] = done[i];
+        if (ms_per_query) ms_per_query[i] = ms[i];
+    }
+    if (num_tried) *num_tried = (uint32_t)done.size();
+    *best = (uint32_t)bi;
+    return apply_tuning(c, &done[bi]);
 }
 
 int wally_sync(wally_ctx *c, void *stream)

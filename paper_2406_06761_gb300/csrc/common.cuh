@@ -58,6 +58,10 @@ struct DevParams {
     u64 rs_inv_s[WALLY_MAX_LIMBS][WALLY_MAX_LIMBS];
     const u32 *slot_pos;      // [N] NTT position (mod t) of slot s
     const DevParams *self;    // device copy of this block (kernels read it there)
+    // launch shape (host side only; no kernel reads these): dynamic shared
+    // memory of the transform kernels (0 = what they need; more caps the CTAs
+    // an SM holds) and resident CTAs per SM of the multiply-accumulate
+    u32 ntt_smem, mac_ctas_per_sm;
 };
 
 __device__ __forceinline__ u64 csub(u64 x, u64 m) { return x >= m ? x - m : x; }

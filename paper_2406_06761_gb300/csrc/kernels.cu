@@ -158,7 +158,9 @@ __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
     __shared__ Mod md;
     const u32 x = blockIdx.x;
     if (x >= item_count(a.n_max, a.n_dev)) return;
-    const int j = blockIdx.y, L = dpp->L;
+    // the CTAs of j = P (which also run two inverse transforms) are
+    // dispatched first, so that the short ones fill the end of the grid
+    const int L = dpp->L, j = L - (int)blockIdx.y;
     load_mod(&md, dpp, j);
     const u64 *kx = a.key + (size_t)(a.key_map ? a.key_map[x] : x) * a.key_stride;
     u64 *dd = a.dd + ((size_t)x * (L + 1) + j) * L * N;
@@ -490,10 +492,15 @@ cudaError_t set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// the transform kernels may be launched with more shared memory than they
+// use (fewer CTAs per SM): up to 226 KB, which with their static shared
+// memory stays within the 227 KB a CTA may opt in to
+constexpr size_t kMaxDynSmem = 226 * 1024;
+
 template <int LOGN>
 cudaError_t set_attrs_logn()
 {
-    const size_t sb = ntt_smem_words<LOGN>() * 8;
+    const size_t sb = kMaxDynSmem;
     cudaError_t e = cudaSuccess;
 #define SA(k) if (e == cudaSuccess) e = set_smem(k<LOGN>, sb)
     SA(k_to_ntt);
@@ -516,7 +523,8 @@ cudaError_t set_attrs_logn()
     default: return cudaErrorInvalidValue;          \
     }
 
-#define SMEM(LG) (ntt_smem_words<LG>() * 8)
+// dynamic shared memory of a transform kernel: its need, or the tuned size
+#define SMEM(LG) (dp.ntt_smem > ntt_smem_words<LG>() * 8 ? (size_t)dp.ntt_smem : (size_t)ntt_smem_words<LG>() * 8)
 static inline int ntt_threads(int log_n) { return (1 << log_n) / 32; }
 
 cudaError_t set_client_kernel_attributes(int log_n);
@@ -533,6 +541,16 @@ cudaError_t set_kernel_attributes(int log_n, u32 g)
     if (e == cudaSuccess) e = set_smem(k_mac<4, 2>, 64 * 1024);
     if (e == cudaSuccess) e = set_smem(k_mac<32, 1>, 64 * 1024);
     return e;
+}
+
+size_t ntt_smem_need(int log_n)
+{
+    switch (log_n) {
+    case 12: return ntt_smem_words<12>() * 8;
+    case 13: return ntt_smem_words<13>() * 8;
+    case 14: return ntt_smem_words<14>() * 8;
+    default: return 0;
+    }
 }
 
 // The parameter block is read from device memory by every kernel.
@@ -605,7 +623,7 @@ cudaError_t launch_mac(const DevParams &dp, const ClusterStore &cs, const WavePl
     // upper bound of work items: segments <= queries in the wave
     const u64 tiles = (u64)dp.n / cs.ts;
     u64 items = (u64)max_wave * m_max * dp.L * tiles;
-    u64 grid = (u64)num_sms * 3;
+    u64 grid = (u64)num_sms * (dp.mac_ctas_per_sm ? dp.mac_ctas_per_sm : 3);
     if (grid > items) grid = items;
     if (grid == 0) return cudaSuccess;
     ProfScope ps(pr, KK_MAC, st);

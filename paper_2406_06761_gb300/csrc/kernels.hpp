@@ -105,6 +105,7 @@ struct EncodeArgs {
     u32 ts;
     u32 *chunk0_out;     // optional [K]: chunk0_out[c] = local index of chunk (c, 0)
 };
+size_t ntt_smem_need(int log_n);  // shared memory a transform kernel needs
 cudaError_t launch_encode_clusters(const DevParams &dp, const EncodeArgs &a, cudaStream_t st, Profiler *pr = nullptr);
 cudaError_t launch_export_cluster(const DevParams &dp, const ClusterStore &cs, u32 cluster, u32 m, u64 *out,
                                   cudaStream_t st);

@@ -48,6 +48,17 @@ class wally_info(ctypes.Structure):
     ]
 
 
+class wally_tuning(ctypes.Structure):
+    _fields_ = [("max_wave", ctypes.c_uint32), ("lanes", ctypes.c_uint32), ("mac_ctas_per_sm", ctypes.c_uint32),
+                ("ntt_ctas_per_sm", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+AUTOTUNE_MAX = 16
+
+
 class wally_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -79,6 +90,11 @@ SIGNATURES = {
     "wally_profile_read": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_u32)]),
     "wally_measure_int_peaks": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "wally_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(wally_tuning)]),
+    "wally_set_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(wally_tuning)]),
+    "wally_autotune": (ctypes.c_int, [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                      _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u32),
+                                      ctypes.POINTER(_u32), _vp]),
     "wally_last_error": (ctypes.c_char_p, []),
 }
 
@@ -267,6 +283,41 @@ def wally_measure_int_peaks(device: int = 0) -> dict:
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().wally_measure_int_peaks(device, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return {"modmul_per_s": a.value, "butterfly_per_s": b.value, "mac128_per_s": c.value}
+
+
+def wally_get_tuning(ctx: int) -> wally_tuning:
+    t = wally_tuning()
+    _check(load().wally_get_tuning(ctx, ctypes.byref(t)))
+    return t
+
+
+def wally_set_tuning(ctx: int, max_wave: int, lanes: int = 2, mac_ctas_per_sm: int = 3,
+                     ntt_ctas_per_sm: int = 0) -> None:
+    t = wally_tuning(max_wave, lanes, mac_ctas_per_sm, ntt_ctas_per_sm)
+    _check(load().wally_set_tuning(ctx, ctypes.byref(t)))
+
+
+def wally_autotune(ctx: int, n: int, cluster_ids, cts, galois_keys, input_index, out_offsets, out,
+                   candidates=None, reps: int = 1, stream=None) -> tuple[int, list]:
+    """Time the sample batch under each candidate shape (dicts or
+    wally_tuning; None = the library's staged search), keep the fastest.
+    Returns (index of the best, [(shape dict, ms per query or -1), ...]) in
+    the order the shapes were timed."""
+    _require_cuda(cluster_ids, cts, galois_keys, input_index, out_offsets, out)
+    if candidates is None:
+        arr, nc, cap = None, 0, AUTOTUNE_MAX
+    else:
+        cs = [c if isinstance(c, wally_tuning) else wally_tuning(**c) for c in candidates]
+        arr = (wally_tuning * len(cs))(*cs)
+        nc = cap = len(cs)
+    tried = (wally_tuning * cap)()
+    ms = (ctypes.c_double * cap)()
+    count, best = _u32(), _u32()
+    _check(load().wally_autotune(ctx, ctypes.cast(arr, _vp) if arr is not None else None, nc, reps, n,
+                                 _ptr(cluster_ids), _ptr(cts), _ptr(galois_keys), _ptr(input_index),
+                                 _ptr(out_offsets), _ptr(out), ctypes.cast(tried, _vp), ms, ctypes.byref(count),
+                                 ctypes.byref(best), _stream(stream)))
+    return best.value, [(tried[i].as_dict(), ms[i]) for i in range(min(count.value, cap))]
 
 
 def wally_last_error() -> str:

@@ -1,0 +1,99 @@
+"""Launch shapes and the autotuner: every shape gives the same bits, the
+autotuner keeps the fastest candidate it timed, and a candidate whose
+workspace cannot be allocated is skipped rather than failing the call."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2406_06761_gb300 import harness as H
+from paper_2406_06761_gb300 import wally as Wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wl():
+    w = H.DeviceWorkload("batched", max_wave=256)
+    yield w
+    w.close()
+
+
+def _run(wl, batch):
+    out = wl.alloc_out(batch[3])
+    out.zero_()
+    wl.eval(batch, out)
+    Wl.wally_sync(wl.ctx.ptr)
+    return out
+
+
+SHAPES = [
+    dict(max_wave=256, lanes=2, mac_ctas_per_sm=3, ntt_ctas_per_sm=0),
+    dict(max_wave=100, lanes=1, mac_ctas_per_sm=1, ntt_ctas_per_sm=1),
+    dict(max_wave=333, lanes=2, mac_ctas_per_sm=2, ntt_ctas_per_sm=2),
+    dict(max_wave=2048, lanes=1, mac_ctas_per_sm=3, ntt_ctas_per_sm=3),
+]
+
+
+def test_every_shape_gives_the_same_outputs(wl):
+    batch = wl.device_batch(0, wl.n)
+    Wl.wally_set_tuning(wl.ctx.ptr, **SHAPES[0])
+    ref = _run(wl, batch)
+    for s in SHAPES[1:]:
+        Wl.wally_set_tuning(wl.ctx.ptr, **s)
+        assert Wl.wally_get_tuning(wl.ctx.ptr).as_dict() == s
+        assert torch.equal(_run(wl, batch), ref), s
+    Wl.wally_set_tuning(wl.ctx.ptr, **SHAPES[0])
+
+
+def test_autotune_keeps_the_fastest(wl):
+    batch = wl.device_batch(0, 600)
+    ids, idx, offs, chunks, _ = batch
+    out = wl.alloc_out(chunks)
+    best, table = Wl.wally_autotune(wl.ctx.ptr, ids.numel(), ids, wl.pool.cts, wl.pool.keys, idx, offs, out,
+                                    candidates=SHAPES, reps=1)
+    ms = [m for _, m in table]
+    assert all(m > 0 for m in ms)
+    assert best == int(np.argmin(ms))
+    assert Wl.wally_get_tuning(wl.ctx.ptr).as_dict() == SHAPES[best]
+    # the outputs of the last timed call are those of any shape
+    Wl.wally_set_tuning(wl.ctx.ptr, **SHAPES[0])
+    assert torch.equal(out, _run(wl, batch))
+
+
+def test_autotune_skips_a_shape_that_does_not_fit(wl):
+    batch = wl.device_batch(0, 64)
+    ids, idx, offs, chunks, _ = batch
+    out = wl.alloc_out(chunks)
+    huge = dict(max_wave=1 << 22, lanes=2, mac_ctas_per_sm=3, ntt_ctas_per_sm=0)  # ~100 TB of workspace
+    best, table = Wl.wally_autotune(wl.ctx.ptr, ids.numel(), ids, wl.pool.cts, wl.pool.keys, idx, offs, out,
+                                    candidates=[huge, SHAPES[0]], reps=1)
+    assert table[0][1] == -1 and table[1][1] > 0 and best == 1
+    assert Wl.wally_get_tuning(wl.ctx.ptr).as_dict() == SHAPES[0]
+
+
+def test_invalid_shapes_are_rejected(wl):
+    for bad in (dict(max_wave=0), dict(max_wave=8, lanes=3), dict(max_wave=8, mac_ctas_per_sm=4)):
+        with pytest.raises(Wl.WallyError) as e:
+            Wl.wally_set_tuning(wl.ctx.ptr, **bad)
+        assert e.value.code == Wl.WALLY_EINVAL
+
+
+def test_staged_search(wl):
+    """Without candidates: wave size x lanes first, then the CTA counts at the
+    best of those; the kept shape is the fastest timed."""
+    batch = wl.device_batch(0, wl.n)
+    ids, idx, offs, chunks, _ = batch
+    out = wl.alloc_out(chunks)
+    best, table = Wl.wally_autotune(wl.ctx.ptr, ids.numel(), ids, wl.pool.cts, wl.pool.keys, idx, offs, out, reps=1)
+    assert len(table) == 9
+    first = table[:6]
+    assert sorted((s["max_wave"], s["lanes"]) for s, _ in first) == [(w, l) for w in (512, 1024, 2048) for l in (1, 2)]
+    ok = [m for _, m in first if m > 0]
+    s1 = first[[m for _, m in first].index(min(ok))][0]
+    for s, _ in table[6:]:
+        assert (s["max_wave"], s["lanes"]) == (s1["max_wave"], s1["lanes"])
+    ms = [m if m > 0 else float("inf") for _, m in table]
+    assert best == int(np.argmin(ms))
+    assert Wl.wally_get_tuning(wl.ctx.ptr).as_dict() == table[best][0]
+    Wl.wally_set_tuning(wl.ctx.ptr, **SHAPES[0])
+    assert torch.equal(out, _run(wl, batch))

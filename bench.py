@@ -509,8 +509,8 @@ def run_e2e(wl, subs, args, dev):
     from paper_2406_06761_gb300 import wally as Wl
     cts_h = wl.pool.cts.cpu().pin_memory()
     keys_h = wl.pool.keys.cpu().pin_memory()
-    # calls of at most ~6 GB of outputs each
-    cap_q = max(1, int(6e9 // (8 * wl.ctw * max(1, int(wl.chunks.max())))))
+    # calls of at most ~16 GB of outputs each
+    cap_q = max(1, int(16e9 // (8 * wl.ctw * max(1, int(wl.chunks.max())))))
     calls = []
     for lo, hi in subs:
         for a in range(lo, hi, cap_q):

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <thread>
 
 #include "../../include/wally.h"
 #include "host_nt.hpp"
@@ -229,6 +230,11 @@ struct wally_ctx {
     DevBuf<u64> stage_ct[2], stage_key[2], stage_out[2];
     DevBuf<u32> stage_cluster[2];
     DevBuf<void *> stage_ptrs[2];
+    PinnedBuf<u64> h_ct[2], h_out[2];
+    PinnedBuf<u32> h_plan32[2];
+    PinnedBuf<void *> h_planptr[2];
+    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
     // client and export temporaries
     DevBuf<u64> tmp;
     DevBuf<u32> tmp32;
@@ -843,7 +849,16 @@ void wally_destroy(wally_ctx *c)
         c->stage_out[b].release();
         c->stage_cluster[b].release();
         c->stage_ptrs[b].release();
+        c->h_ct[b].release();
+        c->h_out[b].release();
+        c->h_plan32[b].release();
+        c->h_planptr[b].release();
+        if (c->in_done[b]) cudaEventDestroy(c->in_done[b]);
+        if (c->comp_done[b]) cudaEventDestroy(c->comp_done[b]);
+        if (c->out_done[b]) cudaEventDestroy(c->out_done[b]);
     }
+    if (c->cin) cudaStreamDestroy(c->cin);
+    if (c->cout) cudaStreamDestroy(c->cout);
     c->tmp.release();
     c->tmp32.release();
     delete c;
@@ -1068,6 +1083,35 @@ int wally_eval_batch(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64
     return eval_device(c, ls, ss, (int)c->lanes_pref, n, ids, cts, keys, input_index, out_offsets, out);
 }
 
+// Copy many host blocks (dst, src, bytes) with a few threads: the small
+// per-query ciphertexts and outputs of the host path are gathered into and
+// scattered from one contiguous pinned buffer a wave, so that each crosses
+// to the device in one large transfer instead of hundreds of small ones.
+struct HostCopy {
+    void *dst;
+    const void *src;
+    size_t bytes;
+};
+
+void parallel_copy(const std::vector<HostCopy> &jobs)
+{
+    const size_t n = jobs.size();
+    if (!n) return;
+    unsigned hw = std::thread::hardware_concurrency();
+    const size_t nt = std::min<size_t>(std::max(1u, std::min(hw, 16u)), (n + 15) / 16);
+    auto work = [&](size_t t) {
+        for (size_t i = t; i < n; i += nt) memcpy(jobs[i].dst, jobs[i].src, jobs[i].bytes);
+    };
+    if (nt <= 1) {
+        work(0);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (size_t t = 1; t < nt; t++) th.emplace_back(work, t);
+    work(0);
+    for (std::thread &x : th) x.join();
+}
+
 int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const uint64_t *cts, const uint64_t *keys,
                           const uint32_t *input_index, const uint64_t *out_offsets, uint64_t *out, void *stream)
 {
@@ -1089,7 +1133,10 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
         if (c->stage_ct[b].ensure((size_t)W * ctw) != cudaSuccess ||
             c->stage_key[b].ensure((size_t)W * keysw) != cudaSuccess ||
             c->stage_out[b].ensure((size_t)W * c->m_max * ctw) != cudaSuccess ||
-            c->stage_cluster[b].ensure(W + 4) != cudaSuccess || c->stage_ptrs[b].ensure(3 * (size_t)W) != cudaSuccess)
+            c->stage_cluster[b].ensure(W + 4) != cudaSuccess || c->stage_ptrs[b].ensure(3 * (size_t)W) != cudaSuccess ||
+            c->h_ct[b].ensure((size_t)W * ctw) != cudaSuccess ||
+            c->h_out[b].ensure((size_t)W * c->m_max * ctw) != cudaSuccess ||
+            c->h_plan32[b].ensure((size_t)W + 4) != cudaSuccess || c->h_planptr[b].ensure(3 * (size_t)W) != cudaSuccess)
             return fail(WALLY_ENOMEM, "cannot allocate the staging buffers");
     }
     // host-side grouping by cluster (counting sort; stable)
@@ -1111,53 +1158,79 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
     } else {
         fixed_waves(n, W, waves);
     }
-    cudaStream_t cin = nullptr, cout_ = nullptr;
-    CUDA_TRY(cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking));
-    CUDA_TRY(cudaStreamCreateWithFlags(&cout_, cudaStreamNonBlocking));
-    cudaEvent_t in_done[2], comp_done[2], out_done[2];
-    for (int b = 0; b < 2; b++) {
-        CUDA_TRY(cudaEventCreateWithFlags(&in_done[b], cudaEventDisableTiming));
-        CUDA_TRY(cudaEventCreateWithFlags(&comp_done[b], cudaEventDisableTiming));
-        CUDA_TRY(cudaEventCreateWithFlags(&out_done[b], cudaEventDisableTiming));
-        CUDA_TRY(cudaEventRecord(comp_done[b], st));
-        CUDA_TRY(cudaEventRecord(out_done[b], st));
+    if (!c->cin) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->cin, cudaStreamNonBlocking));
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->cout, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; b++) {
+            CUDA_TRY(cudaEventCreateWithFlags(&c->in_done[b], cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&c->comp_done[b], cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&c->out_done[b], cudaEventDisableTiming));
+        }
     }
-    // per-buffer host copies of the plan inputs (pinned so the uploads are async)
-    std::vector<uint32_t *> h_plan32(2, nullptr);
-    std::vector<void **> h_planptr(2, nullptr);
+    cudaStream_t cin = c->cin, cout_ = c->cout;
     for (int b = 0; b < 2; b++) {
-        CUDA_TRY(cudaMallocHost(&h_plan32[b], 4 * ((size_t)W + 4)));
-        CUDA_TRY(cudaMallocHost(&h_planptr[b], sizeof(void *) * 3 * (size_t)W));
+        CUDA_TRY(cudaEventRecord(c->in_done[b], st));
+        CUDA_TRY(cudaEventRecord(c->comp_done[b], st));
+        CUDA_TRY(cudaEventRecord(c->out_done[b], st));
     }
-    std::vector<uint32_t> pair_off(W + 1);
+    // per buffer: the wave it holds and its (query, chunk) offsets
+    std::vector<uint32_t> pair_off[2] = {std::vector<uint32_t>(W + 1), std::vector<uint32_t>(W + 1)};
+    int held[2] = {-1, -1};
+    std::vector<HostCopy> jobs;
+    jobs.reserve(W);
+    // outputs of wave w (in buffer w & 1), already read back: to the caller
+    auto scatter = [&](int w) -> int {
+        const int b = w & 1;
+        if (cudaEventSynchronize(c->out_done[b]) != cudaSuccess) return fail(WALLY_ECUDA, "output read-back failed");
+        const Wave &wv = waves[w];
+        jobs.clear();
+        for (uint32_t i = 0; i < wv.len; i++) {
+            const uint32_t q = order[wv.begin + i];
+            const uint32_t m = c->h_chunks[ids[q]];
+            jobs.push_back({out + out_offsets[q] * ctw, c->h_out[b].p + (size_t)pair_off[b][i] * ctw, 8 * ctw * m});
+        }
+        parallel_copy(jobs);
+        held[b] = -1;
+        return WALLY_OK;
+    };
     rc = WALLY_OK;
     for (size_t wave = 0; wave < waves.size() && rc == WALLY_OK; wave++) {
         const int b = wave & 1;
         const uint32_t wb = waves[wave].begin, len = waves[wave].len;
-        // buffer b is free once the compute and the read-back of wave - 2 are done
-        if (cudaEventSynchronize(comp_done[b]) != cudaSuccess) { rc = fail(WALLY_ECUDA, "event sync"); break; }
-        uint32_t *p32 = h_plan32[b];
-        void **pp = h_planptr[b];
+        // the pinned buffers of b are free once the uploads of wave - 2 are
+        // done and its outputs have been handed over
+        if (held[b] >= 0 && (rc = scatter(held[b])) != WALLY_OK) break;
+        if (cudaEventSynchronize(c->in_done[b]) != cudaSuccess) {
+            rc = fail(WALLY_ECUDA, "input upload failed");
+            break;
+        }
+        uint32_t *p32 = c->h_plan32[b].p;
+        void **pp = c->h_planptr[b].p;
+        std::vector<uint32_t> &po = pair_off[b];
         p32[0] = len;
         p32[1] = p32[2] = p32[3] = 0;
-        pair_off[0] = 0;
+        po[0] = 0;
+        jobs.clear();
         for (uint32_t i = 0; i < len; i++) {
             const uint32_t q = order[wb + i];
             const uint32_t src = input_index ? input_index[q] : q;
             p32[4 + i] = ids[q];
-            pair_off[i + 1] = pair_off[i] + c->h_chunks[ids[q]];
+            po[i + 1] = po[i] + c->h_chunks[ids[q]];
             pp[i] = c->stage_ct[b].p + (size_t)i * ctw;
             pp[W + i] = c->stage_key[b].p + (size_t)i * keysw;
-            pp[2 * (size_t)W + i] = c->stage_out[b].p + (size_t)pair_off[i] * ctw;
-            if (cudaMemcpyAsync(c->stage_ct[b].p + (size_t)i * ctw, cts + (size_t)src * ctw, 8 * ctw,
-                                cudaMemcpyHostToDevice, cin) != cudaSuccess ||
-                cudaMemcpyAsync(c->stage_key[b].p + (size_t)i * keysw, keys + (size_t)src * keysw, 8 * keysw,
-                                cudaMemcpyHostToDevice, cin) != cudaSuccess) {
-                rc = fail(WALLY_ECUDA, "input copy failed");
-                break;
-            }
+            pp[2 * (size_t)W + i] = c->stage_out[b].p + (size_t)po[i] * ctw;
+            jobs.push_back({c->h_ct[b].p + (size_t)i * ctw, cts + (size_t)src * ctw, 8 * ctw});
         }
-        if (rc) break;
+        parallel_copy(jobs);
+        // uploads wait until the compute of wave - 2 has read the device buffers
+        CUDA_TRY(cudaStreamWaitEvent(cin, c->comp_done[b], 0));
+        CUDA_TRY(cudaMemcpyAsync(c->stage_ct[b].p, c->h_ct[b].p, 8 * ctw * len, cudaMemcpyHostToDevice, cin));
+        for (uint32_t i = 0; i < len; i++) {
+            const uint32_t q = order[wb + i];
+            const uint32_t src = input_index ? input_index[q] : q;
+            CUDA_TRY(cudaMemcpyAsync(c->stage_key[b].p + (size_t)i * keysw, keys + (size_t)src * keysw, 8 * keysw,
+                                     cudaMemcpyHostToDevice, cin));
+        }
         WavePlan wp = ln.wp;
         wp.counts = c->stage_cluster[b].p;
         wp.cluster = c->stage_cluster[b].p + 4;
@@ -1166,37 +1239,25 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
         wp.dst_out = (u64 **)(c->stage_ptrs[b].p + 2 * (size_t)W);
         CUDA_TRY(cudaMemcpyAsync(wp.counts, p32, 4 * ((size_t)len + 4), cudaMemcpyHostToDevice, cin));
         CUDA_TRY(cudaMemcpyAsync(c->stage_ptrs[b].p, pp, sizeof(void *) * 3 * (size_t)W, cudaMemcpyHostToDevice, cin));
-        CUDA_TRY(cudaEventRecord(in_done[b], cin));
-        CUDA_TRY(cudaStreamWaitEvent(st, in_done[b], 0));
-        CUDA_TRY(cudaStreamWaitEvent(st, out_done[b], 0));
+        CUDA_TRY(cudaEventRecord(c->in_done[b], cin));
+        CUDA_TRY(cudaStreamWaitEvent(st, c->in_done[b], 0));
+        CUDA_TRY(cudaStreamWaitEvent(st, c->out_done[b], 0));
         if (c->compact()) rc = encode_wave(c, ln, waves[wave], ln.zlist.p, zc.size(), st);
         if (rc == WALLY_OK) rc = run_wave(c, ln, wp, len, wave_store(c, ln), st);
         if (rc) break;
-        CUDA_TRY(cudaEventRecord(comp_done[b], st));
-        CUDA_TRY(cudaStreamWaitEvent(cout_, comp_done[b], 0));
-        for (uint32_t i = 0; i < len; i++) {
-            const uint32_t q = order[wb + i];
-            const uint32_t m = c->h_chunks[ids[q]];
-            if (cudaMemcpyAsync(out + out_offsets[q] * ctw, c->stage_out[b].p + (size_t)pair_off[i] * ctw,
-                                8 * ctw * m, cudaMemcpyDeviceToHost, cout_) != cudaSuccess) {
-                rc = fail(WALLY_ECUDA, "output copy failed");
-                break;
-            }
-        }
-        CUDA_TRY(cudaEventRecord(out_done[b], cout_));
+        CUDA_TRY(cudaEventRecord(c->comp_done[b], st));
+        CUDA_TRY(cudaStreamWaitEvent(cout_, c->comp_done[b], 0));
+        CUDA_TRY(cudaMemcpyAsync(c->h_out[b].p, c->stage_out[b].p, 8 * ctw * po[len], cudaMemcpyDeviceToHost, cout_));
+        CUDA_TRY(cudaEventRecord(c->out_done[b], cout_));
+        held[b] = (int)wave;
+    }
+    for (int k = 0; k < 2 && rc == WALLY_OK; k++) {
+        const int b = (int)((waves.size() + k) & 1);  // the older wave first
+        if (held[b] >= 0) rc = scatter(held[b]);
     }
     cudaStreamSynchronize(cin);
     cudaStreamSynchronize(cout_);
     cudaStreamSynchronize(st);
-    for (int b = 0; b < 2; b++) {
-        cudaEventDestroy(in_done[b]);
-        cudaEventDestroy(comp_done[b]);
-        cudaEventDestroy(out_done[b]);
-        cudaFreeHost(h_plan32[b]);
-        cudaFreeHost(h_planptr[b]);
-    }
-    cudaStreamDestroy(cin);
-    cudaStreamDestroy(cout_);
     return rc;
 }
 

@@ -240,7 +240,8 @@ __global__ void NTT_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
     __shared__ Mod md;
     const u32 x = blockIdx.x;
     if (x >= item_count(a.n_max, a.n_dev)) return;
-    const int L = dpp->L, j = blockIdx.y % L, c = blockIdx.y / L;
+    // component 1 first: its CTAs also run the next rotation's digit INTT
+    const int L = dpp->L, j = blockIdx.y % L, c = 1 - (int)(blockIdx.y / L);
     load_mod(&md, dpp, j);
     const u64 q = md.p, P = dpp->m[L].p, half = (P - 1) / 2;
     const u64 pinv = dpp->pinv[j], pinv_s = dpp->pinv_s[j];

@@ -286,3 +286,35 @@ def test_eval_empty_batch_and_errors(tiny):
     fresh.close()
     with pytest.raises(Wl.WallyError):
         Wl.wally_setup_params(11, 2, 36, 17, 192)   # unsupported ring size
+
+
+def test_eval_largest_cluster_and_limit(tiny):
+    """The largest cluster BSGS allows (m = g - 1 = 15 chunks at N = 4096,
+    ragged last chunk), bit for bit against the oracle and decrypted; a
+    cluster of g chunks is rejected (Sec. 5: BSGS while m < sqrt(d))."""
+    w, _, prm = tiny
+    ctx = Wl.Context(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    size = (prm.g - 2) * prm.N + 1
+    E = W.embeddings(size, prm.d, 15, seed=17)
+    Wl.wally_load_clusters(ctx.ptr, np.array([size], np.uint32), E)
+    assert Wl.wally_cluster_chunks(ctx.ptr, 0) == prm.g - 1
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P, seed=17)
+    q = W.query_vectors(1, prm.d, 15, seed=17)[0]
+    keys = O.keygen_pair(prm, cr.secret[0], cr.key_a[0], cr.key_e[0])
+    ct = O.encrypt_query(prm, cr.secret[0], q, cr.enc_a[0], cr.enc_e[0])
+    m = prm.g - 1
+    out = torch.empty((m, 2, prm.L, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_eval_batch(ctx.ptr, 1, torch.zeros(1, dtype=torch.int32, device=DEV), _u64(ct[None]), _u64(keys[None]),
+                        None, torch.zeros(1, dtype=torch.int64, device=DEV), out)
+    Wl.wally_sync(ctx.ptr)
+    got = _np(out)
+    mo, pt = O.encode_cluster(prm, E)
+    assert mo == m
+    assert np.array_equal(got, O.eval_query(prm, m, pt, ct, keys))
+    sc = np.concatenate([O.decrypt_slots(prm, cr.secret[0], got[k]) for k in range(m)])
+    assert np.array_equal(sc[:size], E.astype(np.int64) @ q.astype(np.int64)) and np.all(sc[size:] == 0)
+    with pytest.raises(Wl.WallyError) as ei:
+        Wl.wally_load_clusters(ctx.ptr, np.array([(prm.g - 1) * prm.N + 1], np.uint32),
+                               W.embeddings((prm.g - 1) * prm.N + 1, prm.d, 15, seed=18))
+    assert ei.value.code == Wl.WALLY_EINVAL
+    ctx.close()

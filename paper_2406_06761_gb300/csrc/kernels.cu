@@ -134,9 +134,11 @@ __global__ void NTT_LB(LOGN) k_ks_a(const DevParams *dpp, RotArgs a)
     extern __shared__ u64 smraw[];
     Smem<LOGN> S(smraw);
     __shared__ Mod md;
-    const u32 x = blockIdx.x;
+    // the 2L CTAs of an item are adjacent in the grid (they share its data in L2)
+    const int L = dpp->L;
+    const u32 x = blockIdx.x / (2 * L);
     if (x >= item_count(a.n_max, a.n_dev)) return;
-    const int L = dpp->L, j = blockIdx.y % L, c = blockIdx.y / L;
+    const int y = (int)(blockIdx.x % (2 * L)), j = y % L, c = y / L;
     load_mod(&md, dpp, j);
     poly_load<LOGN>(S.poly, a.src + x * a.src_stride + ((size_t)c * L + j) * N);
     permute_and_digit<LOGN>(S, md, a.galois, c, a.sc + ((size_t)x * 2 * L + c * L + j) * N,
@@ -156,11 +158,13 @@ __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
     extern __shared__ u64 smraw[];
     Smem<LOGN> S(smraw);
     __shared__ Mod md;
-    const u32 x = blockIdx.x;
+    // the L+1 CTAs of an item are adjacent in the grid, so that the digits
+    // they all read are served from L2; within an item the CTA of j = P
+    // (which also runs two inverse transforms) comes first
+    const int L = dpp->L;
+    const u32 x = blockIdx.x / (L + 1);
     if (x >= item_count(a.n_max, a.n_dev)) return;
-    // the CTAs of j = P (which also run two inverse transforms) are
-    // dispatched first, so that the short ones fill the end of the grid
-    const int L = dpp->L, j = L - (int)blockIdx.y;
+    const int j = L - (int)(blockIdx.x % (L + 1));
     load_mod(&md, dpp, j);
     const u64 *kx = a.key + (size_t)(a.key_map ? a.key_map[x] : x) * a.key_stride;
     u64 *dd = a.dd + ((size_t)x * (L + 1) + j) * L * N;
@@ -238,10 +242,13 @@ __global__ void NTT_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
     extern __shared__ u64 smraw[];
     Smem<LOGN> S(smraw);
     __shared__ Mod md;
-    const u32 x = blockIdx.x;
+    // the 2L CTAs of an item are adjacent in the grid (they share the residue
+    // mod P in L2); component 1 first: its CTAs also run the next rotation's
+    // digit INTT
+    const int L = dpp->L;
+    const u32 x = blockIdx.x / (2 * L);
     if (x >= item_count(a.n_max, a.n_dev)) return;
-    // component 1 first: its CTAs also run the next rotation's digit INTT
-    const int L = dpp->L, j = blockIdx.y % L, c = 1 - (int)(blockIdx.y / L);
+    const int y = (int)(blockIdx.x % (2 * L)), j = y % L, c = 1 - y / L;
     load_mod(&md, dpp, j);
     const u64 q = md.p, P = dpp->m[L].p, half = (P - 1) / 2;
     const u64 pinv = dpp->pinv[j], pinv_s = dpp->pinv_s[j];
@@ -602,15 +609,15 @@ cudaError_t launch_rotate(const DevParams &dp, const RotArgs &a, cudaStream_t st
     DISPATCH_LOGN(dp.log_n, ({
                       if (!a.prepared) {
                           ProfScope ps(pr, KK_KS_A, st);
-                          k_ks_a<LG><<<dim3(a.n_max, 2 * L), ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
+                          k_ks_a<LG><<<a.n_max * 2 * L, ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
                       }
                       {
                           ProfScope ps(pr, KK_KS_B, st);
-                          k_ks_b<LG><<<dim3(a.n_max, L + 1), ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
+                          k_ks_b<LG><<<a.n_max * (L + 1), ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
                       }
                       {
                           ProfScope ps(pr, KK_KS_C, st);
-                          k_ks_c<LG><<<dim3(a.n_max, 2 * L), ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
+                          k_ks_c<LG><<<a.n_max * 2 * L, ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
                       }
                   }));
     return cudaGetLastError();

@@ -63,6 +63,7 @@ def _load():
             lib = ctypes.CDLL(build())
             sig = {
                 "or_params_init": (ctypes.c_int, [ctypes.c_uint32] * 5 + [_u64p, ctypes.c_uint64, ctypes.c_uint64, _pp]),
+                "or_params_set_split": (ctypes.c_int, [_pp, ctypes.c_uint32]),
                 "or_is_prime": (ctypes.c_int, [ctypes.c_uint64]),
                 "or_prev_prime_1mod": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
                 "or_smallest_root": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint32]),
@@ -140,8 +141,11 @@ class Params:
 
 @functools.lru_cache(maxsize=None)
 def params(log_n: int, L: int, q_bits: int, t_bits: int, dim: int,
-           q: tuple | None = None, p: int = 0, t: int = 0) -> Params:
-    """Derive the parameter set (primes by trial division, roots by search)."""
+           q: tuple | None = None, p: int = 0, t: int = 0, baby_steps: int = 0) -> Params:
+    """Derive the parameter set (primes by trial division, roots by search).
+    baby_steps: another split g x h of the diagonals (Sec. 5: g = d_pad,
+    h = 1 is the plain diagonal method for clusters of sqrt(d) chunks or
+    more); 0 keeps g = h = sqrt(d_pad)."""
     lib = _load()
     raw = _Params()
     qa = _u64(q) if q else None
@@ -149,6 +153,8 @@ def params(log_n: int, L: int, q_bits: int, t_bits: int, dim: int,
                             ctypes.byref(raw))
     if rc != 0:
         raise ValueError(f"or_params_init failed ({rc})")
+    if baby_steps and lib.or_params_set_split(ctypes.byref(raw), baby_steps) != 0:
+        raise ValueError(f"baby_steps = {baby_steps} does not split d_pad = {raw.d_pad}")
     return Params(raw)
 
 

@@ -179,6 +179,21 @@ int or_params_init(uint32_t logN, uint32_t L, uint32_t q_bits, uint32_t t_bits, 
     return 0;
 }
 
+/* Another split of the diagonals into g baby steps and h = d_pad / g giant
+ * steps.  Sec. 5: the plaintexts are pre-rotated for BSGS only while a
+ * cluster has fewer than sqrt(d) chunks; for larger clusters the query is
+ * rotated through every diagonal with no giant steps, which is the split
+ * g = d_pad, h = 1 (the pre-rotation by g*i is then the identity).  g must be
+ * a power of two dividing d_pad, at least 2. */
+int or_params_set_split(or_params *o, uint32_t g)
+{
+    if (g < 2 || g > o->d_pad || (g & (g - 1)) || o->d_pad % g) return -1;
+    o->g = g;
+    o->h = o->d_pad / g;
+    o->kg = powmod(3, g, 2 * (uint64_t)o->N);
+    return 0;
+}
+
 /* ---------------------------------------------------------------- NTT
  * Negacyclic number-theoretic transform (Sec. 7 "Reducing the computation of
  * BFV operations"): A[i] = sum_k a[k] psi^((2i+1)k), natural order, i.e. the

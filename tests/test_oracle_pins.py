@@ -458,3 +458,48 @@ def test_compressed_tiny_response_decrypts(tiny_params):
     cc = O.compress(prm, out, l0, l1)
     sc = O.decrypt_compressed_slots(prm, cr.secret[0], cc, l0, l1)
     assert np.array_equal(sc[:1024], E.astype(np.int64) @ q.astype(np.int64)) and np.all(sc[1024:] == 0)
+
+
+def test_plain_diagonal_split_bits_match_bigint_small():
+    """The split g = d_pad, h = 1 (Sec. 5: no pre-rotation and no giant steps
+    once a cluster has sqrt(d) chunks or more) at N = 16, d = 4, two chunks,
+    bit for bit against the big-integer restatement, and decrypted."""
+    prm = O.params(4, 2, 30, 10, 4, baby_steps=4)
+    assert (prm.g, prm.h, prm.kg) == (4, 1, pow(3, 4, 32))
+    E = W.embeddings(27, prm.d, 15, seed=19)
+    q = W.query_vectors(1, prm.d, 15, seed=19)[0]
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P, seed=19)
+    keys = O.keygen_pair(prm, cr.secret[0], cr.key_a[0], cr.key_e[0])
+    ct = O.encrypt_query(prm, cr.secret[0], q, cr.enc_a[0], cr.enc_e[0])
+    m, pt = O.encode_cluster(prm, E)
+    assert m == 2
+    got = O.eval_query(prm, m, pt, ct, keys)
+    ref = B.eval_query(prm, pt.tolist(), ct.tolist(), [keys[0].tolist(), keys[1].tolist()])
+    assert got.tolist() == ref
+    sc = np.concatenate([O.decrypt_slots(prm, cr.secret[0], got[k]) for k in range(m)])
+    assert np.array_equal(sc[:27], (E.astype(np.int64) @ q.astype(np.int64) + prm.t // 2) % prm.t - prm.t // 2)
+
+
+def test_plain_diagonal_split_at_sqrt_d_chunks(tiny_params):
+    """A cluster of exactly sqrt(d_pad) = 16 chunks, which BSGS may not take
+    (m < g), evaluated with the plain split g = 256, h = 1: the scores
+    decrypt exactly; the plaintexts of the plain split are the unrotated
+    diagonals, i.e. those of BSGS's first giant step.  (BSGS itself rejects
+    m >= g: test_eval_rejects_too_many_chunks.)"""
+    w = W.WORKLOADS["tiny"]
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim, baby_steps=256)
+    assert (prm.g, prm.h) == (256, 1)
+    n = 16 * prm.N
+    E = W.embeddings(n, w.dim, w.entry_bound, seed=20)
+    q = W.query_vectors(1, w.dim, w.entry_bound, seed=20)[0]
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P, seed=20)
+    keys = O.keygen_pair(prm, cr.secret[0], cr.key_a[0], cr.key_e[0])
+    ct = O.encrypt_query(prm, cr.secret[0], q, cr.enc_a[0], cr.enc_e[0])
+    m, pt = O.encode_cluster(prm, E)
+    assert m == 16
+    got = O.eval_query(prm, m, pt, ct, keys)
+    sc = np.concatenate([O.decrypt_slots(prm, cr.secret[0], got[k]) for k in range(m)])
+    assert np.array_equal(sc, E.astype(np.int64) @ q.astype(np.int64))
+    bsgs = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    m1, pt1 = O.encode_cluster(bsgs, E[:prm.N])
+    assert m1 == 1 and np.array_equal(pt[0, 0, :bsgs.g], pt1[0, 0])

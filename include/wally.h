@@ -71,6 +71,10 @@ typedef struct {
     uint32_t max_wave;     /* queries per internal wave of wally_eval_batch, 0 = 1024 */
     uint32_t store;        /* cluster store: WALLY_STORE_AUTO / _NTT / _COMPACT (below) */
     uint32_t cache_chunks; /* compact store: encoded chunks held per lane, 0 = 16 */
+    uint32_t baby_steps;   /* g of the diagonal split g x h = d_pad: 0 = 2^ceil(log2(d_pad)/2) (BSGS,
+                              Sec. 4.1); d_pad = the plain diagonal method with no giant steps, which
+                              Sec. 5 uses for clusters of sqrt(d) chunks or more (clusters may then have
+                              up to d_pad - 1 chunks); any power of two from 2 to d_pad */
 } wally_params;
 
 /* How wally_load_clusters keeps the clusters.

@@ -775,8 +775,16 @@ int wally_setup_params(const wally_params *prm, wally_ctx **out)
     while (dp < prm->dim) { dp <<= 1; lg++; }
     c->d_pad = dp;
     c->g = 1u << ((lg + 1) / 2);
+    if (prm->baby_steps) {
+        const uint32_t g = prm->baby_steps;
+        if (g < 2 || g > dp || (g & (g - 1))) {
+            delete c;
+            return fail(WALLY_EINVAL, "baby_steps = %u must be a power of two from 2 to d_pad = %u", g, dp);
+        }
+        c->g = g;
+    }
     c->h = dp / c->g;
-    if (c->d_pad > c->N / 2 || c->d_pad > 1024 || c->g < 2) {
+    if (c->d_pad > c->N / 2 || c->d_pad > 1024 || c->d_pad < 4) {
         delete c;
         return fail(WALLY_EINVAL, "dimension %u unsupported (d_pad must be 4..min(1024, N/2))", prm->dim);
     }
@@ -908,7 +916,10 @@ int wally_load_clusters(wally_ctx *c, uint32_t K, const uint32_t *sizes, const i
     for (uint32_t i = 0; i < K; i++) {
         uint32_t m = std::max<uint32_t>(1, (sizes[i] + c->N - 1) / c->N);
         if (m >= c->g)
-            return fail(WALLY_EINVAL, "cluster %u needs %u chunks; BSGS needs fewer than g = %u", i, m, c->g);
+            return fail(WALLY_EINVAL,
+                        "cluster %u needs %u chunks; the diagonal split needs fewer than g = %u "
+                        "(baby_steps = d_pad allows up to d_pad - 1)",
+                        i, m, c->g);
         chunks[i] = m;
         chunk0[i] = (uint32_t)Z;
         row0[i] = rows;

@@ -359,6 +359,60 @@ __global__ void __launch_bounds__(256) k_mac(const DevParams *dpp, ClusterStore 
     }
 }
 
+// The same products for the other splits, mainly those with more than 32 baby
+// steps (the plain diagonal split g = d_pad, h = 1 of Sec. 5 for clusters of
+// sqrt(d) chunks or more): the g ciphertexts are streamed from global memory
+// instead of held in registers; one thread per (slot of the tile, component,
+// query).
+__global__ void __launch_bounds__(256) k_mac_wide(const DevParams *dpp, ClusterStore cs, WavePlan wp, const u64 *ctp,
+                                                  u64 *Tout, u32 m_max)
+{
+    extern __shared__ u64 sm[];
+    __shared__ Mod md;
+    const int L = dpp->L, log_n = dpp->log_n, N = 1 << log_n;
+    const int g = dpp->g, h = dpp->h, dp_ = dpp->d_pad;
+    const int ts = cs.ts, tiles = N / ts;
+    const size_t ctw = (size_t)2 * L * N;
+    const u32 nseg = wp.counts[2];
+    const u64 total = (u64)nseg * m_max * L * tiles;
+    const int slot_in = threadIdx.x % ts;
+    const int rest = threadIdx.x / ts;
+    const int comp = rest & 1, ql = rest >> 1, QL = 128 / ts;
+    for (u64 v = blockIdx.x; v < total; v += gridDim.x) {
+        const int tile = (int)(v % tiles);
+        u64 r = v / tiles;
+        const int l = (int)(r % L);
+        r /= L;
+        const int k = (int)(r % m_max);
+        const u32 seg = (u32)(r / m_max);
+        const u32 cl = wp.seg_cluster[seg];
+        if (k >= (int)cs.chunks[cl]) continue;  // uniform across the CTA
+        __syncthreads();
+        if (threadIdx.x == 0) md = dpp->m[l];
+        const u32 z = cs.chunk0[cl] + k;
+        const uint4 *tsrc = (const uint4 *)(cs.ptxt + (((size_t)z * L + l) * tiles + tile) * ((size_t)dp_ * ts));
+        uint4 *tdst = (uint4 *)sm;
+        const int words2 = dp_ * ts / 2;
+        for (int w = threadIdx.x; w < words2; w += 256) tdst[w] = tsrc[w];
+        __syncthreads();
+        if (ql >= QL) continue;
+        const int s = tile * ts + slot_in;
+        const u32 sb = wp.seg_begin[seg], se = wp.seg_end[seg];
+        for (u32 pos = sb + ql; pos < se; pos += QL) {
+            const u64 *cq = ctp + (size_t)pos * g * ctw + (size_t)comp * L * N + (size_t)l * N + s;
+            const u32 p = wp.pair_off[pos] + k;
+            u64 *to = Tout + (size_t)p * h * ctw + (size_t)comp * L * N + (size_t)l * N + s;
+            for (int i = 0; i < h; i++) {
+                u64 hi = 0, lo = 0;
+                const u64 *prow = sm + (size_t)i * g * ts + slot_in;
+#pragma unroll 8
+                for (int b = 0; b < g; b++) mac128(hi, lo, prow[b * ts], cq[(size_t)b * ctw]);
+                to[(size_t)i * ctw] = mont_redc(hi, lo, md);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- a5: output
 template <int LOGN>
 __global__ void NTT_LB(LOGN) k_output(const DevParams *dpp, WavePlan wp, const u64 *S_, size_t S_stride, u32 n_max)
@@ -548,6 +602,7 @@ cudaError_t set_kernel_attributes(int log_n, u32 g)
     if (e == cudaSuccess) e = set_smem(k_mac<8, 2>, 64 * 1024);
     if (e == cudaSuccess) e = set_smem(k_mac<4, 2>, 64 * 1024);
     if (e == cudaSuccess) e = set_smem(k_mac<32, 1>, 64 * 1024);
+    if (e == cudaSuccess) e = set_smem(k_mac_wide, 64 * 1024);
     return e;
 }
 
@@ -640,7 +695,10 @@ cudaError_t launch_mac(const DevParams &dp, const ClusterStore &cs, const WavePl
     case 8: k_mac<8, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max); break;
     case 16: k_mac<16, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max); break;
     case 32: k_mac<32, 1><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max); break;
-    default: return cudaErrorInvalidValue;
+    default:
+        if (128 % cs.ts) return cudaErrorInvalidValue;
+        k_mac_wide<<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max);
+        break;
     }
     return cudaGetLastError();
 }

@@ -32,6 +32,7 @@ class wally_params(ctypes.Structure):
         ("t_bits", ctypes.c_uint32), ("dim", ctypes.c_uint32), ("device", ctypes.c_int32),
         ("q", ctypes.POINTER(ctypes.c_uint64)), ("p_special", ctypes.c_uint64), ("t", ctypes.c_uint64),
         ("max_wave", ctypes.c_uint32), ("store", ctypes.c_uint32), ("cache_chunks", ctypes.c_uint32),
+        ("baby_steps", ctypes.c_uint32),
     ]
 
 
@@ -157,9 +158,10 @@ def _u64_view(t: torch.Tensor) -> torch.Tensor:
 
 def wally_setup_params(log_n: int, num_q: int, q_bits: int, t_bits: int, dim: int, device: int = 0,
                        q=None, p_special: int = 0, t: int = 0, max_wave: int = 0, store: int = STORE_AUTO,
-                       cache_chunks: int = 0) -> int:
+                       cache_chunks: int = 0, baby_steps: int = 0) -> int:
     lib = load()
-    prm = wally_params(log_n, num_q, q_bits, t_bits, dim, device, None, p_special, t, max_wave, store, cache_chunks)
+    prm = wally_params(log_n, num_q, q_bits, t_bits, dim, device, None, p_special, t, max_wave, store, cache_chunks,
+                       baby_steps)
     qarr = None
     if q is not None:
         qarr = (ctypes.c_uint64 * len(q))(*q)

@@ -318,3 +318,44 @@ def test_eval_largest_cluster_and_limit(tiny):
                                W.embeddings((prm.g - 1) * prm.N + 1, prm.d, 15, seed=18))
     assert ei.value.code == Wl.WALLY_EINVAL
     ctx.close()
+
+
+@pytest.mark.parametrize("store", [Wl.STORE_NTT, Wl.STORE_COMPACT])
+def test_eval_plain_diagonal_split(tiny, store):
+    """baby_steps = d_pad (g = 256, h = 1: the plain diagonal method Sec. 5
+    uses for clusters of sqrt(d) chunks or more): a 16-chunk cluster, which
+    BSGS rejects, and small clusters, bit for bit against the oracle with the
+    same split; ragged waves of 3 queries."""
+    w, _, _ = tiny
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim, baby_steps=256)
+    ctx = Wl.Context(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim, max_wave=3, baby_steps=256, store=store)
+    assert (ctx.info.g, ctx.info.h, int(ctx.info.kg)) == (256, 1, prm.kg)
+    sizes = np.array([16 * prm.N, 1000, prm.N + 1], np.uint32)
+    E = W.embeddings(int(sizes.sum()), w.dim, w.entry_bound, seed=21)
+    Wl.wally_load_clusters(ctx.ptr, sizes, E)
+    assert [Wl.wally_cluster_chunks(ctx.ptr, c) for c in range(3)] == [16, 1, 2]
+    ids = np.array([0, 2, 1, 0], np.uint32)
+    cr = W.client_randomness(4, prm.N, prm.q, prm.P, seed=21)
+    qs = W.query_vectors(4, w.dim, w.entry_bound, seed=21)
+    keys = np.stack([O.keygen_pair(prm, cr.secret[i], cr.key_a[i], cr.key_e[i]) for i in range(4)])
+    cts = np.stack([O.encrypt_query(prm, cr.secret[i], qs[i] if i < 3 else None, cr.enc_a[i], cr.enc_e[i])
+                    for i in range(4)])
+    m = np.array([16, 1, 2])[ids]
+    offs = np.concatenate([[0], np.cumsum(m)[:-1]]).astype(np.int64)
+    out = torch.full((int(m.sum()), 2, prm.L, prm.N), -1, dtype=torch.int64, device=DEV)
+    Wl.wally_eval_batch(ctx.ptr, 4, torch.from_numpy(ids.astype(np.int32)).to(DEV), _u64(cts), _u64(keys), None,
+                        torch.from_numpy(offs).to(DEV), out)
+    Wl.wally_sync(ctx.ptr)
+    got = _np(out)
+    row0 = np.concatenate([[0], np.cumsum(sizes.astype(np.int64))[:-1]])
+    enc = {c: O.encode_cluster(prm, E[int(row0[c]):int(row0[c] + sizes[c])]) for c in (1, 2)}
+    for q in (1, 2):  # the small clusters, against the oracle's evaluation
+        c = int(ids[q])
+        mc, pt = enc[c]
+        assert np.array_equal(got[offs[q]:offs[q] + mc], O.eval_query(prm, mc, pt, cts[q], keys[q])), q
+    # the 16-chunk cluster: query 0 bit for bit, query 3 (a fake) decrypts to zeros
+    m0, pt0 = O.encode_cluster(prm, E[:int(sizes[0])])
+    assert np.array_equal(got[0:16], O.eval_query(prm, m0, pt0, cts[0], keys[0]))
+    sc = np.concatenate([O.decrypt_slots(prm, cr.secret[3], got[offs[3] + k]) for k in range(16)])
+    assert np.all(sc == 0)
+    ctx.close()

@@ -426,3 +426,91 @@ def decrypt_compressed_slots(prm: Params, s, cc, l0: int, l1: int) -> np.ndarray
     m = np.array([((t * int(v) + q // 2) // q) % t for v in x], dtype=np.uint64)
     v = slots_decode(prm, m).astype(np.int64)
     return np.where(v > t // 2, v - t, v)
+
+
+# ------------------------------------------------------------------ index PIR (Sec. 4.2)
+# The server side of the index PIR under the keyword PIR of Sec. 4.2
+# ("Details of keyword PIR", MulPIR): oblivious expansion of the query
+# ciphertext into indicator ciphertexts (substitutions, i.e. Galois
+# automorphisms X -> X^(N/2^a + 1) followed by key switching, plus additions
+# and a monomial shift), then the first dimension: d2 sums of d1
+# plaintext-ciphertext products.  Coefficient form throughout.
+
+def pir_galois(prm: Params, a: int) -> int:
+    """Galois element of expansion level a: N/2^a + 1 (Sec. 4.2, "Reducing
+    evaluation key size")."""
+    return prm.N // (1 << a) + 1
+
+
+def pir_query_plaintext(prm: Params, row: int, levels: int) -> np.ndarray:
+    """The client's query plaintext: (2^levels)^-1 mod t times X^row, so that
+    after `levels` expansion levels ciphertext `row` encrypts 1 and every
+    other one 0."""
+    m = np.zeros(prm.N, np.uint64)
+    m[row] = pow(1 << levels, -1, prm.t)
+    return m
+
+
+def _ct_add(prm: Params, a, b, sign: int = 1) -> np.ndarray:
+    out = np.empty((2, prm.L, prm.N), np.uint64)
+    for c in range(2):
+        for l, q in enumerate(prm.q):
+            x = a[c, l].astype(object)
+            y = b[c, l].astype(object)
+            out[c, l] = ((x + y) % q if sign > 0 else (x - y) % q).astype(np.uint64)
+    return out
+
+
+def monomial_shift(prm: Params, ct, e: int) -> np.ndarray:
+    """ct * X^(-e) in Z_q[X]/(X^N + 1): coefficient n moves to n - e; those
+    that wrap below 0 move to n - e + N with their sign flipped (X^-N = -1)."""
+    ct = _u64(ct)
+    out = np.empty_like(ct)
+    N = prm.N
+    for c in range(2):
+        for l, q in enumerate(prm.q):
+            x = ct[c, l]
+            out[c, l, :N - e] = x[e:]
+            out[c, l, N - e:] = (np.uint64(q) - x[:e]) % np.uint64(q)
+    return out
+
+
+def pir_expand(prm: Params, ct, keys, levels: int) -> np.ndarray:
+    """Oblivious expansion (Angel et al., used by MulPIR): at level a every
+    ciphertext C becomes C + sigma(C) (kept at index i) and
+    (C - sigma(C)) X^(-2^a) (index i + 2^a), sigma = substitution by
+    N/2^a + 1 with keys[a].  Returns [2^levels][2][L][N]."""
+    cur = [_u64(ct)]
+    for a in range(levels):
+        k = pir_galois(prm, a)
+        half = len(cur)
+        nxt = [None] * (2 * half)
+        for i, C in enumerate(cur):
+            S = rotate(prm, k, keys[a], C)
+            nxt[i] = _ct_add(prm, C, S, +1)
+            nxt[i + half] = monomial_shift(prm, _ct_add(prm, C, S, -1), 1 << a)
+        cur = nxt
+    return np.stack(cur)
+
+
+def lift_plaintext(prm: Params, m) -> np.ndarray:
+    """A plaintext polynomial (coefficients in [0, t)) lifted centred into
+    every ciphertext modulus (reading R9): [L][N]."""
+    m = _u64(m).astype(np.int64)
+    t = prm.t
+    v = np.where(m > (t - 1) // 2, m - t, m)
+    return np.stack([(v % q).astype(np.uint64) for q in prm.q])
+
+
+def pir_first_dimension(prm: Params, db, indicators) -> np.ndarray:
+    """MulPIR's first dimension: out[j] = sum_i db[i][j] * indicators[i]
+    (PtCtMult + CtCtAdd), db [d1][d2][N] coefficients in [0, t).
+    Returns [d2][2][L][N]."""
+    db = _u64(db)
+    d1, d2 = db.shape[0], db.shape[1]
+    ind = _u64(indicators)[:d1]
+    out = np.empty((d2, 2, prm.L, prm.N), np.uint64)
+    for j in range(d2):
+        pts = np.stack([lift_plaintext(prm, db[i, j]) for i in range(d1)])
+        out[j] = ptct_sum(prm, pts, ind)
+    return out

@@ -184,3 +184,32 @@ def client_randomness(n: int, N: int, q: list[int], P: int, seed: int = 0, index
         enc_a=uniform_residues((n,), list(q), N, seed, tag + "/ea"),
         enc_e=errors((n, N), seed, tag + "/ee"),
     )
+
+
+@dataclasses.dataclass
+class PirClientRandomness:
+    """What a PIR client draws: a secret, one substitution key per expansion
+    level (uniform a, small errors), and the query encryption's a and e."""
+    secret: np.ndarray   # int8 [n][N]
+    key_a: np.ndarray    # uint64 [n][levels][L][L+1][N]
+    key_e: np.ndarray    # int8 [n][levels][L][N]
+    enc_a: np.ndarray    # uint64 [n][L][N]
+    enc_e: np.ndarray    # int8 [n][N]
+
+
+def pir_client_randomness(n: int, levels: int, N: int, q: list[int], P: int, seed: int = 0,
+                          index: int = 0) -> PirClientRandomness:
+    L = len(q)
+    tag = f"pir{index}"
+    return PirClientRandomness(
+        secret=ternary(n, N, seed, tag + "/s"),
+        key_a=uniform_residues((n, levels, L), list(q) + [P], N, seed, tag + "/ka"),
+        key_e=errors((n, levels, L, N), seed, tag + "/ke"),
+        enc_a=uniform_residues((n,), list(q), N, seed, tag + "/ea"),
+        enc_e=errors((n, N), seed, tag + "/ee"),
+    )
+
+
+def pir_plaintexts(rows: int, cols: int, N: int, t: int, seed: int = 0) -> np.ndarray:
+    """A PIR table of uniform plaintext coefficients in [0, t): [rows][cols][N]."""
+    return stream(seed, "pir_table").integers(0, t, size=(rows, cols, N), dtype=np.uint64)

@@ -503,3 +503,94 @@ def test_plain_diagonal_split_at_sqrt_d_chunks(tiny_params):
     bsgs = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
     m1, pt1 = O.encode_cluster(bsgs, E[:prm.N])
     assert m1 == 1 and np.array_equal(pt[0, 0, :bsgs.g], pt1[0, 0])
+
+
+# ---------------------------------------------------------------- index PIR (Sec. 4.2)
+
+def _pir_keys(prm, cr, levels):
+    return [O.keygen(prm, cr.secret[0], O.pir_galois(prm, a), cr.key_a[0, a], cr.key_e[0, a]) for a in range(levels)]
+
+
+def test_pir_expansion_bits_match_bigint_small(small_params):
+    """Two expansion levels at N = 16, bit for bit against a big-integer
+    restatement (substitution = big-integer Rot_k; add, subtract and the
+    monomial X^-e over Z_Q)."""
+    prm = small_params
+    levels = 2
+    cr = W.pir_client_randomness(1, levels, prm.N, prm.q, prm.P, seed=41)
+    keys = _pir_keys(prm, cr, levels)
+    ct = O.encrypt(prm, cr.secret[0], O.pir_query_plaintext(prm, 3, levels), cr.enc_a[0], cr.enc_e[0])
+    got = O.pir_expand(prm, ct, keys, levels)
+
+    def shift(c, e):
+        out = []
+        for comp in range(2):
+            limbs = []
+            for l, q in enumerate(prm.q):
+                x = [int(v) for v in c[comp][l]]
+                limbs.append([x[n + e] if n + e < prm.N else (-x[n + e - prm.N]) % q for n in range(prm.N)])
+            out.append(limbs)
+        return out
+
+    def sub(a, b):
+        return [[[(int(x) - int(y)) % prm.q[l] for x, y in zip(a[c][l], b[c][l])] for l in range(prm.L)]
+                for c in range(2)]
+
+    cur = [ct.tolist()]
+    for a in range(levels):
+        k = O.pir_galois(prm, a)
+        nxt = [None] * (2 * len(cur))
+        for i, C in enumerate(cur):
+            S = B.rotate(prm, k, keys[a].tolist(), C)
+            nxt[i] = B.add(prm, C, S)
+            nxt[i + len(cur)] = shift(sub(C, S), 1 << a)
+        cur = nxt
+    assert got.tolist() == cur
+
+
+def test_pir_expansion_decrypts_to_indicators(tiny_params):
+    """Expanding (2^c)^-1 X^row over c = 3 levels gives 8 ciphertexts; number
+    `row` decrypts to the constant 1 and every other one to 0."""
+    prm = tiny_params
+    levels, row = 3, 5
+    cr = W.pir_client_randomness(1, levels, prm.N, prm.q, prm.P, seed=42)
+    keys = _pir_keys(prm, cr, levels)
+    ct = O.encrypt(prm, cr.secret[0], O.pir_query_plaintext(prm, row, levels), cr.enc_a[0], cr.enc_e[0])
+    ind = O.pir_expand(prm, ct, keys, levels)
+    assert ind.shape[0] == 8
+    for k in range(8):
+        m, _ = O.decrypt_poly(prm, cr.secret[0], ind[k])
+        want = np.zeros(prm.N, np.int64)
+        want[0] = 1 if k == row else 0
+        assert np.array_equal(np.asarray(m, np.int64), want), k
+
+
+def test_pir_first_dimension_returns_the_row(tiny_params):
+    """The first dimension over a 6 x 3 table (rows padded to 8 indicators):
+    column j decrypts to the plaintext at (row, j), coefficient for
+    coefficient."""
+    prm = tiny_params
+    levels, row = 3, 4
+    db = W.pir_plaintexts(6, 3, prm.N, prm.t, seed=43)
+    cr = W.pir_client_randomness(1, levels, prm.N, prm.q, prm.P, seed=43)
+    keys = _pir_keys(prm, cr, levels)
+    ct = O.encrypt(prm, cr.secret[0], O.pir_query_plaintext(prm, row, levels), cr.enc_a[0], cr.enc_e[0])
+    out = O.pir_first_dimension(prm, db, O.pir_expand(prm, ct, keys, levels))
+    for j in range(3):
+        m, _ = O.decrypt_poly(prm, cr.secret[0], out[j])
+        assert np.array_equal(np.asarray(m, np.uint64), db[row, j]), j
+
+
+def test_monomial_shift_is_negacyclic(small_params):
+    """X^-e times a polynomial equals the negacyclic product with the
+    coefficient vector of X^(N-e) times -1 (schoolbook)."""
+    prm = small_params
+    rng = np.random.default_rng(44)
+    ct = np.stack([np.stack([rng.integers(0, q, prm.N, dtype=np.uint64) for q in prm.q]) for _ in range(2)])
+    for e in (1, 3, 8):
+        got = O.monomial_shift(prm, ct, e)
+        for c in range(2):
+            for l, q in enumerate(prm.q):
+                mono = np.zeros(prm.N, np.uint64)
+                mono[prm.N - e] = q - 1  # X^-e = -X^(N-e)
+                assert np.array_equal(got[c, l], O.polymul_schoolbook(prm, l, ct[c, l], mono)), (e, c, l)

@@ -241,6 +241,57 @@ int wally_compress_responses(wally_ctx *ctx, uint32_t n, const uint64_t *cts, ui
 int wally_decrypt_compressed(wally_ctx *ctx, uint32_t n, const int8_t *secret, const uint32_t *secret_index,
                              const uint8_t *packed, int64_t *scores, void *stream);
 
+/* ---------------------------------------------------------------- metadata: index PIR
+ * The keyword PIR of Sec. 4.2 ("Details of keyword PIR") fetches the metadata
+ * of one entry of a cluster: entries sit in two cuckoo tables (split tables:
+ * one for each hash function), each table is a d1 x d2 matrix of plaintexts,
+ * and the client runs an index PIR on each table (MulPIR).  The server side
+ * of that index PIR built here is its query expansion and its first
+ * dimension: the query ciphertext encrypts (2^c)^-1 X^row (c levels,
+ * 2^c >= d1); the server expands it obliviously into 2^c ciphertexts (level
+ * a: C -> C + sigma(C) and (C - sigma(C)) X^(-2^a), sigma the substitution
+ * X -> X^(N/2^a + 1) with the client's key for it), so that ciphertext i
+ * encrypts [i == row]; the answer is, per column j, sum_i table[i][j] *
+ * ciphertext i, which decrypts to table[row][j].  MulPIR's second dimension
+ * (ciphertext x ciphertext products) is not part of this library: the answer
+ * holds all d2 columns. */
+
+/* Load the table: host uint64_t [rows][cols][N], plaintext coefficients in
+ * [0, t).  rows (d1) 1..4096, cols (d2) >= 1.  The table is lifted centred
+ * into the ciphertext moduli, kept in NTT form (device, rows*cols*L*N*8
+ * bytes), and replaces any previous table.  Expansion levels c =
+ * ceil(log2 rows).  Synchronises `stream`.
+ * Errors: WALLY_EINVAL (sizes, a coefficient >= t), WALLY_ENOMEM, WALLY_ECUDA. */
+int wally_pir_load(wally_ctx *ctx, uint32_t rows, uint32_t cols, const uint64_t *table, void *stream);
+
+/* Answer n queries (all device buffers, coefficient form):
+ *   queries  uint64_t [n][2][L][N]                 the clients' query ciphertexts
+ *   keys     uint64_t [n][c][L][2][L+1][N]         per query, the key of N/2^a + 1 for level a < c
+ *   out      uint64_t [n][cols][2][L][N]           column j of query q: table[row_q][j]
+ * Asynchronous on `stream`; works on up to 8 queries at a time in scratch the
+ * context owns (about 5 * 2^c ciphertexts a query at L = 3, plus its keys and
+ * answer).
+ * Errors: WALLY_ESTATE (no table), WALLY_EINVAL, WALLY_ENOMEM, WALLY_ECUDA. */
+int wally_pir_answer(wally_ctx *ctx, uint32_t n, const uint64_t *queries, const uint64_t *keys, uint64_t *out,
+                     void *stream);
+
+/* Client side of the PIR.  Galois keys for a list of elements (at most 16):
+ * galois (host) [num_keys], odd, < 2N; key_a device [n][num_keys][L][L+1][N],
+ * key_e device int8 [n][num_keys][L][N]; keys device [n][num_keys][L][2][L+1][N]
+ * (the same relation as wally_keygen). */
+int wally_keygen_galois(wally_ctx *ctx, uint32_t n, uint32_t num_keys, const uint64_t *galois, const int8_t *secret,
+                        const uint64_t *key_a, const int8_t *key_e, uint64_t *keys, void *stream);
+
+/* Encrypt plaintext polynomials m (device uint64_t [n][N], coefficients in
+ * [0, t)) as in wally_encrypt_query (no slot encoding): cts [n][2][L][N]. */
+int wally_encrypt_poly(wally_ctx *ctx, uint32_t n, const int8_t *secret, const uint64_t *m, const uint64_t *enc_a,
+                       const int8_t *enc_e, uint64_t *cts, void *stream);
+
+/* Decrypt to plaintext coefficients: coeffs device int64_t [n][N] in [0, t);
+ * ciphertext i uses secret[secret_index ? secret_index[i] : i].  Synchronous. */
+int wally_decrypt_poly(wally_ctx *ctx, uint32_t n, const int8_t *secret, const uint32_t *secret_index,
+                       const uint64_t *cts, int64_t *coeffs, void *stream);
+
 /* ---------------------------------------------------------------- measurement
  * Per-launch device time of the evaluation kernels, taken with CUDA events
  * recorded on the launch stream around every launch (observability; the

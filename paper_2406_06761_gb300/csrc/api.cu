@@ -14,6 +14,7 @@
 #include "host_nt.hpp"
 #include "kernels.hpp"
 #include "ctx_access.hpp"
+#include "pir.hpp"
 
 using namespace wally;
 
@@ -238,6 +239,11 @@ struct wally_ctx {
     // client and export temporaries
     DevBuf<u64> tmp;
     DevBuf<u32> tmp32;
+    // index PIR: the table (NTT form, times 2^64), the monomials X^(-2^a),
+    // and the expansion scratch
+    uint32_t pir_rows = 0, pir_cols = 0, pir_levels = 0;
+    DevBuf<u64> pir_db, pir_mono, pir_E[2], pir_S, pir_keys, pir_out, pir_sc, pir_dg, pir_u, pir_dd;
+    DevBuf<u32> pir_map;
     // optional per-launch timing
     bool prof_on = false;
     EventProfiler prof;
@@ -869,6 +875,10 @@ void wally_destroy(wally_ctx *c)
     if (c->cout) cudaStreamDestroy(c->cout);
     c->tmp.release();
     c->tmp32.release();
+    for (DevBuf<u64> *b : {&c->pir_db, &c->pir_mono, &c->pir_E[0], &c->pir_E[1], &c->pir_S, &c->pir_keys, &c->pir_out,
+                           &c->pir_sc, &c->pir_dg, &c->pir_u, &c->pir_dd})
+        b->release();
+    c->pir_map.release();
     delete c;
 }
 
@@ -1415,6 +1425,152 @@ int wally_autotune(wally_ctx *c, const wally_tuning *cand, uint32_t nc, uint32_t
     if (num_tried) *num_tried = (uint32_t)done.size();
     *best = (uint32_t)bi;
     return apply_tuning(c, &done[bi]);
+}
+
+// ---------------------------------------------------------------- index PIR (Sec. 4.2)
+int wally_pir_load(wally_ctx *c, uint32_t rows, uint32_t cols, const uint64_t *table, void *stream)
+{
+    if (!c || !table) return fail(WALLY_EINVAL, "null argument");
+    if (rows < 1 || rows > 4096 || cols < 1) return fail(WALLY_EINVAL, "table of %u x %u (rows 1..4096)", rows, cols);
+    if ((uint64_t)cols * c->L > 65535) return fail(WALLY_EINVAL, "too many columns");
+    const uint64_t t = c->mods[c->L + 1];
+    const size_t N = c->N, L = c->L, P = (size_t)rows * cols;
+    for (size_t i = 0; i < P * N; i++)
+        if (table[i] >= t) return fail(WALLY_EINVAL, "table coefficient %zu is not below t", i);
+    uint32_t levels = 0;
+    while ((1u << levels) < rows) levels++;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->pir_rows = c->pir_cols = c->pir_levels = 0;
+    c->pir_db.release();
+    DevBuf<u64> raw;
+    if (raw.ensure(P * N) != cudaSuccess || c->pir_db.ensure(P * L * N) != cudaSuccess ||
+        c->pir_mono.ensure(std::max<size_t>(levels, 1) * L * N) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the PIR table (%.2f GB)", P * L * N * 8.0 / 1e9);
+    CUDA_TRY(cudaMemcpyAsync(raw.p, table, 8 * P * N, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(launch_pir_lift(c->dp, raw.p, (u32)P, c->pir_db.p, st));
+    CUDA_TRY(launch_to_ntt(c->dp, nullptr, c->pir_db.p, L * N, c->pir_db.p, L * N, (u32)L, (u32)L, (u32)P, nullptr,
+                           true, st));
+    // X^(-2^a) = -X^(N - 2^a): its NTT per limb, times 2^64
+    std::vector<uint64_t> mono(std::max<size_t>(levels, 1) * L * N, 0);
+    for (uint32_t a = 0; a < levels; a++)
+        for (size_t l = 0; l < L; l++) mono[((size_t)a * L + l) * N + (N - (1u << a))] = c->mods[l] - 1;
+    if (levels) {
+        CUDA_TRY(cudaMemcpyAsync(c->pir_mono.p, mono.data(), 8 * mono.size(), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, c->pir_mono.p, L * N, c->pir_mono.p, L * N, (u32)L, (u32)L, levels,
+                               nullptr, true, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    raw.release();
+    c->pir_rows = rows;
+    c->pir_cols = cols;
+    c->pir_levels = levels;
+    return WALLY_OK;
+}
+
+int wally_pir_answer(wally_ctx *c, uint32_t n, const uint64_t *queries, const uint64_t *keys, uint64_t *out,
+                     void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (!c->pir_rows) return fail(WALLY_ESTATE, "no PIR table loaded");
+    if (n == 0) return WALLY_OK;
+    if (!queries || !out || (c->pir_levels && !keys)) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t lv = c->pir_levels, cols = c->pir_cols, rows = c->pir_rows;
+    const size_t N = c->N, L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
+    const uint32_t chunk = std::min<uint32_t>(n, 8), full = 1u << lv, half = std::max(1u, full / 2);
+    const size_t items = (size_t)chunk * half;
+    if (c->pir_E[0].ensure((size_t)chunk * full * ctw) != cudaSuccess ||
+        c->pir_E[1].ensure((size_t)chunk * full * ctw) != cudaSuccess || c->pir_S.ensure(items * ctw) != cudaSuccess ||
+        c->pir_keys.ensure((size_t)chunk * std::max(lv, 1u) * keyw) != cudaSuccess ||
+        c->pir_out.ensure((size_t)chunk * cols * ctw) != cudaSuccess || c->pir_sc.ensure(items * ctw) != cudaSuccess ||
+        c->pir_dg.ensure(items * L * N) != cudaSuccess || c->pir_u.ensure(items * 2 * (L + 1) * N) != cudaSuccess ||
+        c->pir_dd.ensure(items * (L + 1) * L * N) != cudaSuccess || c->pir_map.ensure(items) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the PIR scratch");
+    for (uint32_t q0 = 0; q0 < n; q0 += chunk) {
+        const uint32_t nq = std::min(chunk, n - q0);
+        // queries and keys to NTT form (keys times 2^64)
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, queries + (size_t)q0 * ctw, ctw, c->pir_E[0].p, ctw, 2 * (u32)L,
+                               (u32)L, nq, nullptr, false, st));
+        if (lv)
+            CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)q0 * lv * keyw, keyw, c->pir_keys.p, keyw,
+                                   2 * (u32)(L * (L + 1)), (u32)(L + 1), nq * lv, nullptr, true, st));
+        int cur = 0;
+        for (uint32_t a = 0; a < lv; a++) {
+            const u32 count = nq << a;
+            CUDA_TRY(launch_pir_qmap(c->pir_map.p, count, a, st));
+            RotArgs r;
+            memset(&r, 0, sizeof(r));
+            r.src = c->pir_E[cur].p;
+            r.src_stride = ctw;
+            r.dst = c->pir_S.p;
+            r.dst_stride = ctw;
+            r.key = c->pir_keys.p + (size_t)a * keyw;
+            r.key_stride = (size_t)lv * keyw;
+            r.key_map = c->pir_map.p;
+            r.n_max = count;
+            r.galois = (uint64_t)(N >> a) + 1;
+            r.sc = c->pir_sc.p;
+            r.dg = c->pir_dg.p;
+            r.u = c->pir_u.p;
+            r.dd = c->pir_dd.p;
+            CUDA_TRY(launch_rotate(c->dp, r, st, c->pr()));
+            CUDA_TRY(launch_pir_combine(c->dp, c->pir_E[cur].p, c->pir_S.p, c->pir_E[cur ^ 1].p,
+                                        c->pir_mono.p + (size_t)a * L * N, count, a, st));
+            cur ^= 1;
+        }
+        CUDA_TRY(launch_pir_dim1(c->dp, c->pir_db.p, rows, cols, c->pir_E[cur].p, full, nq, c->pir_out.p, st));
+        CUDA_TRY(launch_from_ntt(c->dp, c->pir_out.p, out + (size_t)q0 * cols * ctw, 2 * (u32)L, (u32)L, nq * cols,
+                                 st));
+    }
+    return WALLY_OK;
+}
+
+int wally_keygen_galois(wally_ctx *c, uint32_t n, uint32_t nk, const uint64_t *galois, const int8_t *secret,
+                        const uint64_t *key_a, const int8_t *key_e, uint64_t *keys, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0 || nk == 0) return WALLY_OK;
+    if (nk > 16) return fail(WALLY_EINVAL, "at most 16 keys at a time");
+    if (!galois || !secret || !key_a || !key_e || !keys) return fail(WALLY_EINVAL, "null argument");
+    KinvList kl;
+    memset(&kl, 0, sizeof(kl));
+    kl.nk = (int)nk;
+    const uint64_t two_n = 2 * (uint64_t)c->N;
+    for (uint32_t i = 0; i < nk; i++) {
+        if ((galois[i] & 1) == 0 || galois[i] >= two_n) return fail(WALLY_EINVAL, "Galois element %u invalid", i);
+        kl.v[i] = inv_mod_2n(galois[i], two_n);
+    }
+    DeviceGuard guard(c->device);
+    CUDA_TRY(launch_keygen_list(c->dp, secret, key_a, key_e, n, kl, keys, (cudaStream_t)stream));
+    return WALLY_OK;
+}
+
+int wally_encrypt_poly(wally_ctx *c, uint32_t n, const int8_t *secret, const uint64_t *m, const uint64_t *enc_a,
+                       const int8_t *enc_e, uint64_t *cts, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0) return WALLY_OK;
+    if (!secret || !m || !enc_a || !enc_e || !cts) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(launch_encrypt(c->dp, secret, m, enc_a, enc_e, n, cts, (cudaStream_t)stream));
+    return WALLY_OK;
+}
+
+int wally_decrypt_poly(wally_ctx *c, uint32_t n, const int8_t *secret, const uint32_t *secret_index,
+                       const uint64_t *cts, int64_t *coeffs, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0) return WALLY_OK;
+    if (!secret || !cts || !coeffs) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (c->tmp.ensure((size_t)n * c->L * c->N) != cudaSuccess) return fail(WALLY_ENOMEM, "temporary");
+    CUDA_TRY(launch_decrypt_coeffs(c->dp, secret, secret_index, cts, n, c->tmp.p, coeffs, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return WALLY_OK;
 }
 
 int wally_sync(wally_ctx *c, void *stream)

@@ -5,6 +5,7 @@
 // cluster encoding also runs on the server path, when the compact cluster
 // store encodes each wave's chunks on the fly.
 #include "kernels.hpp"
+#include "pir.hpp"
 
 namespace wally {
 
@@ -221,7 +222,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_encrypt(const DevParams *dpp, const int8_t *
 //   b = -a*s + e + [i == j] P s'  (mod q_j),  b = -a*s + e (mod P).
 template <int LOGN>
 __global__ void NTT_LB_WIDE(LOGN) k_keygen(const DevParams *dpp, const int8_t *secret, const u64 *key_a,
-                                      const int8_t *key_e, u64 k1_inv, u64 kg_inv, u64 *keys)
+                                      const int8_t *key_e, KinvList kl, u64 *keys)
 {
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
@@ -230,23 +231,23 @@ __global__ void NTT_LB_WIDE(LOGN) k_keygen(const DevParams *dpp, const int8_t *s
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int j = blockIdx.y, L = dpp->L;
-    const int kk = blockIdx.z / L, i = blockIdx.z % L;
+    const int kk = blockIdx.z / L, i = blockIdx.z % L, NK = kl.nk;
     load_mod(&md, dpp, j);
     const u64 p = md.p;
     const int8_t *s = secret + (size_t)n * N;
     u64 sv[32];
     secret_ntt<LOGN>(sm, sv, s, md, twf);
-    const u64 *a = key_a + ((((size_t)n * 2 + kk) * L + i) * (L + 1) + j) * N;
+    const u64 *a = key_a + ((((size_t)n * NK + kk) * L + i) * (L + 1) + j) * N;
 #pragma unroll 8
     for (int u = 0; u < 32; u++) {
         const int e = threadIdx.x + T * u;
         sm[spos(e)] = a[e];
     }
     poly_times_secret<LOGN>(sm, sv, md, twf, twi);
-    const int8_t *ee = key_e + (((size_t)n * 2 + kk) * L + i) * N;
-    u64 *kb = keys + (((((size_t)n * 2 + kk) * L + i) * 2 + 0) * (L + 1) + j) * N;
-    u64 *ka = keys + (((((size_t)n * 2 + kk) * L + i) * 2 + 1) * (L + 1) + j) * N;
-    const u64 kinv = kk ? kg_inv : k1_inv;
+    const int8_t *ee = key_e + (((size_t)n * NK + kk) * L + i) * N;
+    u64 *kb = keys + (((((size_t)n * NK + kk) * L + i) * 2 + 0) * (L + 1) + j) * N;
+    u64 *ka = keys + (((((size_t)n * NK + kk) * L + i) * 2 + 1) * (L + 1) + j) * N;
+    const u64 kinv = kl.v[kk];
     const u32 mask2n = 2 * N - 1;
 #pragma unroll 4
     for (int u = 0; u < 32; u++) {
@@ -304,7 +305,7 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_residues(const DevParams *dpp, const
 // mod q_l, t x / Q = sum_l y_l t / q_l - (a multiple of t), so m is the
 // rounded sum of the integer parts and the 64-bit fractions of y_l t / q_l.
 template <int LOGN>
-__global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u64 *xs, int64_t *scores)
+__global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u64 *xs, int64_t *scores, bool slots)
 {
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
@@ -330,7 +331,9 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u6
         }
         const u64 rnd = (u64)((frac + ((unsigned __int128)1 << 63)) >> 64);
         sm[spos(e)] = (ipart + rnd) % t;
+        if (!slots) scores[(size_t)n * N + e] = (int64_t)((ipart + rnd) % t);  // coefficient e of m, in [0, t)
     }
+    if (!slots) return;
     ntt_fwd<LOGN>(sm, twf, md);
     for (int u = 0; u < 32; u++) {
         const int s = threadIdx.x + T * u;
@@ -552,10 +555,20 @@ cudaError_t launch_encrypt(const DevParams &dp, const int8_t *secret, const u64 
 cudaError_t launch_keygen(const DevParams &dp, const int8_t *secret, const u64 *key_a, const int8_t *key_e, u32 n,
                           u64, u64, u64 k1_inv, u64 kg_inv, u64 *keys, cudaStream_t st)
 {
-    if (n == 0) return cudaSuccess;
+    KinvList kl;
+    kl.nk = 2;
+    kl.v[0] = k1_inv;
+    kl.v[1] = kg_inv;
+    return launch_keygen_list(dp, secret, key_a, key_e, n, kl, keys, st);
+}
+
+cudaError_t launch_keygen_list(const DevParams &dp, const int8_t *secret, const u64 *key_a, const int8_t *key_e,
+                               u32 n, const KinvList &kl, u64 *keys, cudaStream_t st)
+{
+    if (n == 0 || kl.nk <= 0) return cudaSuccess;
     const DevParams *dpp = device_params_of(dp);
-    DISPATCH_LOGN(dp.log_n, (k_keygen<LG><<<dim3(n, dp.L + 1, 2 * dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
-                                dpp, secret, key_a, key_e, k1_inv, kg_inv, keys)));
+    DISPATCH_LOGN(dp.log_n, (k_keygen<LG><<<dim3(n, dp.L + 1, kl.nk * dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
+                                dpp, secret, key_a, key_e, kl, keys)));
     return cudaGetLastError();
 }
 
@@ -567,7 +580,20 @@ cudaError_t launch_decrypt(const DevParams &dp, const int8_t *secret, const u32 
     DISPATCH_LOGN(dp.log_n, ({
                       k_decrypt_residues<LG><<<dim3(n, dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
                           dpp, secret, secret_index, cts, xs);
-                      k_decrypt_scale<LG><<<n, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, xs, scores);
+                      k_decrypt_scale<LG><<<n, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, xs, scores, true);
+                  }));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decrypt_coeffs(const DevParams &dp, const int8_t *secret, const u32 *secret_index, const u64 *cts,
+                                  u32 n, u64 *xs, int64_t *coeffs, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const DevParams *dpp = device_params_of(dp);
+    DISPATCH_LOGN(dp.log_n, ({
+                      k_decrypt_residues<LG><<<dim3(n, dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
+                          dpp, secret, secret_index, cts, xs);
+                      k_decrypt_scale<LG><<<n, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, xs, coeffs, false);
                   }));
     return cudaGetLastError();
 }

@@ -91,6 +91,11 @@ SIGNATURES = {
     "wally_profile_read": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_u32)]),
     "wally_measure_int_peaks": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "wally_pir_load": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp]),
+    "wally_pir_answer": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp]),
+    "wally_keygen_galois": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "wally_encrypt_poly": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "wally_decrypt_poly": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "wally_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(wally_tuning)]),
     "wally_set_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(wally_tuning)]),
     "wally_autotune": (ctypes.c_int, [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -285,6 +290,37 @@ def wally_measure_int_peaks(device: int = 0) -> dict:
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().wally_measure_int_peaks(device, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return {"modmul_per_s": a.value, "butterfly_per_s": b.value, "mac128_per_s": c.value}
+
+
+def wally_pir_load(ctx: int, table, stream=None) -> None:
+    """table: uint64 numpy array [rows][cols][N] (host), coefficients in [0, t)."""
+    import numpy as np
+    table = np.ascontiguousarray(table, dtype=np.uint64)
+    _check(load().wally_pir_load(ctx, table.shape[0], table.shape[1], table.ctypes.data, _stream(stream)))
+
+
+def wally_pir_answer(ctx: int, n: int, queries, keys, out, stream=None) -> None:
+    _require_cuda(queries, keys, out)
+    _check(load().wally_pir_answer(ctx, n, _ptr(queries), _ptr(keys), _ptr(out), _stream(stream)))
+
+
+def wally_keygen_galois(ctx: int, n: int, galois, secret, key_a, key_e, keys, stream=None) -> None:
+    _require_cuda(secret, key_a, key_e, keys)
+    g = (ctypes.c_uint64 * len(galois))(*[int(x) for x in galois])
+    _check(load().wally_keygen_galois(ctx, n, len(galois), ctypes.cast(g, _vp), _ptr(secret), _ptr(key_a),
+                                      _ptr(key_e), _ptr(keys), _stream(stream)))
+
+
+def wally_encrypt_poly(ctx: int, n: int, secret, m, enc_a, enc_e, cts, stream=None) -> None:
+    _require_cuda(secret, m, enc_a, enc_e, cts)
+    _check(load().wally_encrypt_poly(ctx, n, _ptr(secret), _ptr(m), _ptr(enc_a), _ptr(enc_e), _ptr(cts),
+                                     _stream(stream)))
+
+
+def wally_decrypt_poly(ctx: int, n: int, secret, secret_index, cts, coeffs, stream=None) -> None:
+    _require_cuda(secret, secret_index, cts, coeffs)
+    _check(load().wally_decrypt_poly(ctx, n, _ptr(secret), _ptr(secret_index), _ptr(cts), _ptr(coeffs),
+                                     _stream(stream)))
 
 
 def wally_get_tuning(ctx: int) -> wally_tuning:

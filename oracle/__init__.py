@@ -64,6 +64,7 @@ def _load():
             sig = {
                 "or_params_init": (ctypes.c_int, [ctypes.c_uint32] * 5 + [_u64p, ctypes.c_uint64, ctypes.c_uint64, _pp]),
                 "or_params_set_split": (ctypes.c_int, [_pp, ctypes.c_uint32]),
+                "or_relinkey": (None, [_pp, _i8p, _u64p, _i8p, _u64p]),
                 "or_is_prime": (ctypes.c_int, [ctypes.c_uint64]),
                 "or_prev_prime_1mod": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
                 "or_smallest_root": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint32]),
@@ -514,3 +515,114 @@ def pir_first_dimension(prm: Params, db, indicators) -> np.ndarray:
         pts = np.stack([lift_plaintext(prm, db[i, j]) for i in range(d1)])
         out[j] = ptct_sum(prm, pts, ind)
     return out
+
+
+# ------------------------------------------------------------------ ciphertext products (MulPIR's second dimension)
+# BFV multiplication (Sec. 2 CtCtMult; used by MulPIR's second dimension,
+# Sec. 4.2): the tensor of the centred lifts over Z[X]/(X^N + 1), scaled by
+# t/Q and rounded, then relinearised with the key switching key from s^2 to s.
+# The exact integer tensor is formed from negacyclic products modulo enough
+# extra primes, composed by the Chinese remainder theorem with Python
+# integers.
+
+def relin_keygen(prm: Params, s, a_rand, e_rand) -> np.ndarray:
+    """Key switching key from s^2 to s, layout [L][2][L+1][N]."""
+    s, a_rand, e_rand = _i8(s), _u64(a_rand), _i8(e_rand)
+    out = np.empty((prm.L, 2, prm.L + 1, prm.N), np.uint64)
+    _load().or_relinkey(prm.ptr, _p(s, _i8p), _p(a_rand, _u64p), _p(e_rand, _i8p), _p(out, _u64p))
+    return out
+
+
+def _centred(prm: Params, limbs) -> list[int]:
+    """Integers in (-Q/2, Q/2] from residues [L][N] (CRT)."""
+    Q = prm.Q
+    out = [0] * prm.N
+    for l, q in enumerate(prm.q):
+        Ml = Q // q
+        c = Ml * pow(Ml % q, -1, q)
+        x = limbs[l]
+        for n in range(prm.N):
+            out[n] += int(x[n]) * c
+    half = Q // 2
+    return [v % Q - Q if v % Q > half else v % Q for v in out]
+
+
+def _ext_params(prm: Params, bound_bits: int) -> Params:
+    """The ciphertext primes followed by further primes = 1 mod 2N below P,
+    enough that their product exceeds 2^bound_bits."""
+    qs, below, bits = list(prm.q), prm.P, 0
+    for q in prm.q:
+        bits += q.bit_length() - 1
+    while bits <= bound_bits:
+        below = prev_prime_1mod(below, 2 * prm.N)
+        qs.append(below)
+        bits += below.bit_length() - 1
+    return params(prm.log_n, len(qs), 61, 10, prm.d, q=tuple(qs), t=prm.t)
+
+
+def tensor(prm: Params, pairs) -> list[list[int]]:
+    """sum over (a, b) in pairs of (A0 B0, A0 B1 + A1 B0, A1 B1), exact integer
+    negacyclic products of the centred lifts A, B."""
+    bound = (len(pairs) * prm.N).bit_length() + 2 * prm.Q.bit_length() + 2
+    ext = _ext_params(prm, bound)
+    R = ext.Q
+    acc = [[np.zeros(prm.N, np.uint64) for _ in ext.q] for _ in range(3)]
+    for a, b in pairs:
+        A = [_centred(prm, _u64(a)[c]) for c in range(2)]
+        Bv = [_centred(prm, _u64(b)[c]) for c in range(2)]
+        for j, p in enumerate(ext.q):
+            Ar = [np.array([v % p for v in A[c]], np.uint64) for c in range(2)]
+            Br = [np.array([v % p for v in Bv[c]], np.uint64) for c in range(2)]
+            prods = [polymul(ext, j, Ar[0], Br[0]),
+                     (polymul(ext, j, Ar[0], Br[1]).astype(object) + polymul(ext, j, Ar[1], Br[0]).astype(object)) % p,
+                     polymul(ext, j, Ar[1], Br[1])]
+            for k in range(3):
+                acc[k][j] = ((acc[k][j].astype(object) + np.asarray(prods[k]).astype(object)) % p).astype(np.uint64)
+    out = []
+    for k in range(3):
+        vals = [0] * prm.N
+        for j, p in enumerate(ext.q):
+            Mj = R // p
+            c = Mj * pow(Mj % p, -1, p)
+            x = acc[k][j]
+            for n in range(prm.N):
+                vals[n] += int(x[n]) * c
+        out.append([v % R - R if v % R > R // 2 else v % R for v in vals])
+    return out
+
+
+def scale_round(prm: Params, T: list[int]) -> np.ndarray:
+    """round(t T / Q) mod q_l (halves rounded up): [L][N]."""
+    Q, t = prm.Q, prm.t
+    v = [(2 * t * x + Q) // (2 * Q) for x in T]
+    return np.stack([np.array([x % q for x in v], np.uint64) for q in prm.q])
+
+
+def relinearize(prm: Params, c3, rlk) -> np.ndarray:
+    """(c0, c1, c2) -> (c0, c1) + key switch of c2 from s^2 to s: the hybrid
+    key switch of Rot with the identity automorphism (k = 1)."""
+    c3 = _u64(c3)
+    r = rotate(prm, 1, rlk, np.stack([c3[0], c3[2]]))
+    return _ct_add(prm, r, np.stack([np.zeros_like(c3[1]), c3[1]]), +1)
+
+
+def mul_relin(prm: Params, a, b, rlk) -> np.ndarray:
+    T = tensor(prm, [(a, b)])
+    return relinearize(prm, np.stack([scale_round(prm, T[k]) for k in range(3)]), rlk)
+
+
+def pir_second_dimension(prm: Params, first, col_ind, rlk) -> np.ndarray:
+    """MulPIR's second dimension: sum_j first[j] x col_ind[j] with the
+    tensors summed before the one rescaling and the one relinearisation."""
+    T = tensor(prm, list(zip(_u64(first), _u64(col_ind))))
+    return relinearize(prm, np.stack([scale_round(prm, T[k]) for k in range(3)]), rlk)
+
+
+def pir_query_plaintext2(prm: Params, row: int, col: int, d1: int, levels: int) -> np.ndarray:
+    """A two-dimensional query: (2^levels)^-1 (X^row + X^(d1 + col)); after
+    expansion, ciphertext row and ciphertext d1 + col encrypt 1."""
+    m = np.zeros(prm.N, np.uint64)
+    inv = pow(1 << levels, -1, prm.t)
+    m[row] = inv
+    m[d1 + col] = (int(m[d1 + col]) + inv) % prm.t
+    return m

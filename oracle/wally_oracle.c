@@ -421,6 +421,38 @@ void or_keygen(const or_params *o, const int8_t *s, uint64_t k, const uint64_t *
     free(as);
 }
 
+/* Relinearisation key (the key switching key from s^2 to s): as or_keygen
+ * with s' = s^2, the negacyclic square of the secret, in place of
+ * sigma_k(s):  b_i = -a_i*s + e_i + [i == j] P s^2 (mod q_j),  b_i = -a_i*s + e_i (mod P). */
+void or_relinkey(const or_params *o, const int8_t *s, const uint64_t *a_rand, const int8_t *e_rand, uint64_t *key)
+{
+    uint32_t N = o->N, L = o->L;
+    uint64_t *sj = (uint64_t *)malloc(8 * (size_t)N), *s2 = (uint64_t *)malloc(8 * (size_t)N);
+    uint64_t *as = (uint64_t *)malloc(8 * (size_t)N);
+    for (uint32_t j = 0; j <= L; j++) {
+        uint64_t p = o->mod[j];
+        for (uint32_t n = 0; n < N; n++) sj[n] = smod(s[n], p);
+        or_polymul(o, j, sj, sj, s2);
+        uint64_t Pmod = o->mod[L] % p;
+        for (uint32_t i = 0; i < L; i++) {
+            const uint64_t *a = a_rand + ((size_t)i * (L + 1) + j) * N;
+            const int8_t *e = e_rand + (size_t)i * N;
+            uint64_t *b_out = key + (((size_t)i * 2 + 0) * (L + 1) + j) * N;
+            uint64_t *a_out = key + (((size_t)i * 2 + 1) * (L + 1) + j) * N;
+            or_polymul(o, j, a, sj, as);
+            for (uint32_t n = 0; n < N; n++) {
+                uint64_t v = submod(smod(e[n], p), as[n], p);
+                if (j == i) v = addmod(v, mulmod(Pmod, s2[n], p), p);
+                b_out[n] = v;
+                a_out[n] = a[n] % p;
+            }
+        }
+    }
+    free(sj);
+    free(s2);
+    free(as);
+}
+
 /* Encryption (R1): c1 = a, c0 = -a*s + e + Delta*m (mod q_i), m in [0, t). */
 void or_encrypt(const or_params *o, const int8_t *s, const uint64_t *m_poly, const uint64_t *a_rand,
                 const int8_t *e, uint64_t *ct)

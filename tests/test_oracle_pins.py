@@ -594,3 +594,104 @@ def test_monomial_shift_is_negacyclic(small_params):
                 mono = np.zeros(prm.N, np.uint64)
                 mono[prm.N - e] = q - 1  # X^-e = -X^(N-e)
                 assert np.array_equal(got[c, l], O.polymul_schoolbook(prm, l, ct[c, l], mono)), (e, c, l)
+
+
+# ---------------------------------------------------------------- ciphertext products (MulPIR's second dimension)
+
+def _schoolbook_z(a, b):
+    """Exact negacyclic product over Z (no reduction)."""
+    N = len(a)
+    out = [0] * N
+    for x in range(N):
+        for y in range(N):
+            k = x + y
+            if k < N:
+                out[k] += a[x] * b[y]
+            else:
+                out[k - N] -= a[x] * b[y]
+    return out
+
+
+def test_mul_relin_bits_match_bigint_small(small_params):
+    """At N = 16: the tensor of the centred lifts by schoolbook products over
+    Z, round(t T / Q) by integer division, and the relinearisation as the
+    big-integer key switch of c2 (Rot with k = 1) plus c1 -- bit for bit."""
+    prm = small_params
+    cr = W.client_randomness(2, prm.N, prm.q, prm.P, seed=61)
+    rng = np.random.default_rng(61)
+    ma, mb = (rng.integers(0, prm.t, prm.N, dtype=np.uint64) for _ in range(2))
+    a = O.encrypt(prm, cr.secret[0], ma, cr.enc_a[0], cr.enc_e[0])
+    b = O.encrypt(prm, cr.secret[0], mb, cr.enc_a[1], cr.enc_e[1])
+    rlk = O.relin_keygen(prm, cr.secret[0], cr.key_a[0, 0], cr.key_e[0, 0])
+    got = O.mul_relin(prm, a, b, rlk)
+    Q, t = prm.Q, prm.t
+
+    def lift(ct, c):
+        z = B.poly_crt(ct[c].tolist(), prm.q)
+        return [v - Q if v > Q // 2 else v for v in z]
+
+    A = [lift(a, c) for c in range(2)]
+    Bb = [lift(b, c) for c in range(2)]
+    T = [_schoolbook_z(A[0], Bb[0]),
+         [x + y for x, y in zip(_schoolbook_z(A[0], Bb[1]), _schoolbook_z(A[1], Bb[0]))],
+         _schoolbook_z(A[1], Bb[1])]
+    c3 = [[[((2 * t * v + Q) // (2 * Q)) % q for v in T[k]] for q in prm.q] for k in range(3)]
+    assert np.array_equal(np.stack([O.scale_round(prm, O.tensor(prm, [(a, b)])[k]) for k in range(3)]),
+                          np.array(c3, np.uint64))
+    r = B.rotate(prm, 1, rlk.tolist(), [c3[0], c3[2]])
+    ref = B.add(prm, r, [[[0] * prm.N for _ in prm.q], c3[1]])
+    assert got.tolist() == ref
+    m, _ = O.decrypt_poly(prm, cr.secret[0], got)
+    assert np.array_equal(np.asarray(m, np.uint64), O.polymul(prm, prm.L + 1, ma, mb))
+
+
+def test_relin_key_relation(small_params):
+    """b_i + a_i s = e_i + [i == j] P s^2 on every limb j of the key."""
+    prm = small_params
+    cr = W.client_randomness(1, prm.N, prm.q, prm.P, seed=62)
+    s = cr.secret[0]
+    key = O.relin_keygen(prm, s, cr.key_a[0, 0], cr.key_e[0, 0])
+    mods = prm.q + [prm.P]
+    for i in range(prm.L):
+        for j, p in enumerate(mods):
+            sj = np.array([int(v) % p for v in s], np.uint64)
+            lhs = (key[i, 0, j].astype(object) + O.polymul_schoolbook(prm, j, key[i, 1, j], sj).astype(object)) % p
+            e = np.array([int(v) % p for v in cr.key_e[0, 0, i]], dtype=object)
+            s2 = O.polymul_schoolbook(prm, j, sj, sj).astype(object)
+            want = (e + ((prm.P % p) * s2 if i == j else 0)) % p
+            assert np.array_equal(lhs, want), (i, j)
+
+
+def test_mul_relin_decrypts_to_product(tiny_params):
+    """N = 4096, two 36-bit limbs: the relinearised product of two fresh
+    ciphertexts decrypts to the negacyclic product of their plaintexts mod t."""
+    prm = tiny_params
+    cr = W.client_randomness(2, prm.N, prm.q, prm.P, seed=63)
+    rng = np.random.default_rng(63)
+    ma, mb = (rng.integers(0, prm.t, prm.N, dtype=np.uint64) for _ in range(2))
+    a = O.encrypt(prm, cr.secret[0], ma, cr.enc_a[0], cr.enc_e[0])
+    b = O.encrypt(prm, cr.secret[0], mb, cr.enc_a[1], cr.enc_e[1])
+    rlk = O.relin_keygen(prm, cr.secret[0], cr.key_a[0, 0], cr.key_e[0, 0])
+    m, _ = O.decrypt_poly(prm, cr.secret[0], O.mul_relin(prm, a, b, rlk))
+    assert np.array_equal(np.asarray(m, np.uint64), O.polymul(prm, prm.L + 1, ma, mb))
+
+
+def test_pir_two_dimensions_batched_params():
+    """MulPIR end to end at N = 8192, three 50-bit limbs: a 4 x 2 table, one
+    query ciphertext for (row 2, column 1), expanded over 3 levels into 8
+    indicators (rows 0..3, then columns), first dimension, second dimension
+    with one rescaling and one relinearisation: decrypts to table[2][1]."""
+    w = W.WORKLOADS["batched"]
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    d1, d2, levels, row, col = 4, 2, 3, 2, 1
+    db = W.pir_plaintexts(d1, d2, prm.N, prm.t, seed=64)
+    cr = W.pir_client_randomness(1, levels, prm.N, prm.q, prm.P, seed=64)
+    keys = _pir_keys(prm, cr, levels)
+    rc = W.client_randomness(1, prm.N, prm.q, prm.P, seed=65)
+    rlk = O.relin_keygen(prm, cr.secret[0], rc.key_a[0, 0], rc.key_e[0, 0])
+    ct = O.encrypt(prm, cr.secret[0], O.pir_query_plaintext2(prm, row, col, d1, levels), cr.enc_a[0], cr.enc_e[0])
+    ind = O.pir_expand(prm, ct, keys, levels)
+    first = O.pir_first_dimension(prm, db, ind[:d1])
+    ans = O.pir_second_dimension(prm, first, ind[d1:d1 + d2], rlk)
+    m, _ = O.decrypt_poly(prm, cr.secret[0], ans)
+    assert np.array_equal(np.asarray(m, np.uint64), db[row, col])

@@ -252,9 +252,14 @@ int wally_decrypt_compressed(wally_ctx *ctx, uint32_t n, const int8_t *secret, c
  * a: C -> C + sigma(C) and (C - sigma(C)) X^(-2^a), sigma the substitution
  * X -> X^(N/2^a + 1) with the client's key for it), so that ciphertext i
  * encrypts [i == row]; the answer is, per column j, sum_i table[i][j] *
- * ciphertext i, which decrypts to table[row][j].  MulPIR's second dimension
- * (ciphertext x ciphertext products) is not part of this library: the answer
- * holds all d2 columns. */
+ * ciphertext i, which decrypts to table[row][j] (wally_pir_answer, one
+ * dimension: the answer holds all d2 columns).  wally_pir_answer2 adds
+ * MulPIR's second dimension: the query encrypts (2^c)^-1 (X^row + X^(d1+col))
+ * with 2^c >= d1 + d2, the expansion also yields the column indicators, and
+ * the answer is one ciphertext, sum_j column_j x indicator_(d1+j), formed by
+ * BFV ciphertext products (Sec. 2 CtCtMult: the tensor of the centred lifts,
+ * scaled by t/Q and rounded; the d2 tensors are summed before the one
+ * rescaling and the one relinearisation). */
 
 /* Load the table: host uint64_t [rows][cols][N], plaintext coefficients in
  * [0, t).  rows (d1) 1..4096, cols (d2) >= 1.  The table is lifted centred
@@ -274,6 +279,28 @@ int wally_pir_load(wally_ctx *ctx, uint32_t rows, uint32_t cols, const uint64_t 
  * Errors: WALLY_ESTATE (no table), WALLY_EINVAL, WALLY_ENOMEM, WALLY_ECUDA. */
 int wally_pir_answer(wally_ctx *ctx, uint32_t n, const uint64_t *queries, const uint64_t *keys, uint64_t *out,
                      void *stream);
+
+/* MulPIR with both dimensions (see above): one answer ciphertext a query.
+ *   queries     uint64_t [n][2][L][N]           encrypting (2^c)^-1 (X^row + X^(d1+col))
+ *   keys        uint64_t [n][c][L][2][L+1][N]   c = ceil(log2(rows + cols)) substitution keys
+ *   relin_keys  uint64_t [n][L][2][L+1][N]      wally_keygen_relin
+ *   out         uint64_t [n][2][L][N]           decrypts to table[row][col]
+ * The exact tensor is formed in an extension basis of L + K primes (K chosen
+ * so that their product exceeds 2^(log2 N + 13) Q; L + K <= 7, so L <= 3 at
+ * 50-bit limbs).  rows + cols <= 4096.  Asynchronous on `stream` after a
+ * one-time set-up of the extension basis.  The noise of a product needs
+ * log2(Q / t) well above log2(t N) + the noise of the operands: the
+ * N = 8192, three 50-bit limb parameters qualify, N = 4096 with two 36-bit
+ * limbs do not.
+ * Errors: WALLY_ESTATE (no table), WALLY_EINVAL (sizes, L), WALLY_ENOMEM, WALLY_ECUDA. */
+int wally_pir_answer2(wally_ctx *ctx, uint32_t n, const uint64_t *queries, const uint64_t *keys,
+                      const uint64_t *relin_keys, uint64_t *out, void *stream);
+
+/* Relinearisation keys (key switching from s^2 to s): key_a device
+ * [n][L][L+1][N], key_e device int8 [n][L][N]; keys device [n][L][2][L+1][N]
+ * with b_i = -a_i s + e_i + [i == j] P s^2 (mod q_j), b_i = -a_i s + e_i (mod P). */
+int wally_keygen_relin(wally_ctx *ctx, uint32_t n, const int8_t *secret, const uint64_t *key_a, const int8_t *key_e,
+                       uint64_t *keys, void *stream);
 
 /* Client side of the PIR.  Galois keys for a list of elements (at most 16):
  * galois (host) [num_keys], odd, < 2N; key_a device [n][num_keys][L][L+1][N],

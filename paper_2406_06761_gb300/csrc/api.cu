@@ -241,9 +241,14 @@ struct wally_ctx {
     DevBuf<u32> tmp32;
     // index PIR: the table (NTT form, times 2^64), the monomials X^(-2^a),
     // and the expansion scratch
-    uint32_t pir_rows = 0, pir_cols = 0, pir_levels = 0;
+    uint32_t pir_rows = 0, pir_cols = 0, pir_levels = 0, pir_levels2 = 0;
     DevBuf<u64> pir_db, pir_mono, pir_E[2], pir_S, pir_keys, pir_out, pir_sc, pir_dg, pir_u, pir_dd;
     DevBuf<u32> pir_map;
+    // MulPIR's second dimension: the extension basis (its own context for
+    // the transforms), its constants on the device, and the buffers
+    wally_ctx *ext = nullptr;
+    DevBuf<ExtConst> ext_const;
+    DevBuf<u64> pd_first, pd_col, pd_A, pd_B, pd_T, pd_X, pd_add, pd_out, pd_rlk;
     // optional per-launch timing
     bool prof_on = false;
     EventProfiler prof;
@@ -708,6 +713,54 @@ void release_waves(wally_ctx *c)
     }
 }
 
+// Oblivious expansion of nq queries over lv levels: pir_E[0] holds their
+// NTT-form ciphertexts and pir_keys their keys (NTT form); on return
+// pir_E[cur] holds [nq][2^lv] indicator ciphertexts.
+int pir_expand(wally_ctx *c, uint32_t nq, uint32_t lv, int &cur, cudaStream_t st)
+{
+    const size_t N = c->N, L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
+    cur = 0;
+    for (uint32_t a = 0; a < lv; a++) {
+        const u32 count = nq << a;
+        CUDA_TRY(launch_pir_qmap(c->pir_map.p, count, a, st));
+        RotArgs r;
+        memset(&r, 0, sizeof(r));
+        r.src = c->pir_E[cur].p;
+        r.src_stride = ctw;
+        r.dst = c->pir_S.p;
+        r.dst_stride = ctw;
+        r.key = c->pir_keys.p + (size_t)a * keyw;
+        r.key_stride = (size_t)lv * keyw;
+        r.key_map = c->pir_map.p;
+        r.n_max = count;
+        r.galois = (uint64_t)(N >> a) + 1;
+        r.sc = c->pir_sc.p;
+        r.dg = c->pir_dg.p;
+        r.u = c->pir_u.p;
+        r.dd = c->pir_dd.p;
+        CUDA_TRY(launch_rotate(c->dp, r, st, c->pr()));
+        CUDA_TRY(launch_pir_combine(c->dp, c->pir_E[cur].p, c->pir_S.p, c->pir_E[cur ^ 1].p,
+                                    c->pir_mono.p + (size_t)a * L * N, count, a, st));
+        cur ^= 1;
+    }
+    return WALLY_OK;
+}
+
+int pir_scratch(wally_ctx *c, uint32_t chunk, uint32_t lv, uint32_t cols)
+{
+    const size_t N = c->N, L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
+    const uint32_t full = 1u << lv, half = std::max(1u, full / 2);
+    const size_t items = std::max<size_t>((size_t)chunk * half, chunk);
+    if (c->pir_E[0].ensure((size_t)chunk * full * ctw) != cudaSuccess ||
+        c->pir_E[1].ensure((size_t)chunk * full * ctw) != cudaSuccess || c->pir_S.ensure(items * ctw) != cudaSuccess ||
+        c->pir_keys.ensure((size_t)chunk * std::max(lv, 1u) * keyw) != cudaSuccess ||
+        c->pir_out.ensure((size_t)chunk * cols * ctw) != cudaSuccess || c->pir_sc.ensure(items * ctw) != cudaSuccess ||
+        c->pir_dg.ensure(items * L * N) != cudaSuccess || c->pir_u.ensure(items * 2 * (L + 1) * N) != cudaSuccess ||
+        c->pir_dd.ensure(items * (L + 1) * L * N) != cudaSuccess || c->pir_map.ensure(items) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the PIR scratch");
+    return WALLY_OK;
+}
+
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
@@ -876,9 +929,12 @@ void wally_destroy(wally_ctx *c)
     c->tmp.release();
     c->tmp32.release();
     for (DevBuf<u64> *b : {&c->pir_db, &c->pir_mono, &c->pir_E[0], &c->pir_E[1], &c->pir_S, &c->pir_keys, &c->pir_out,
-                           &c->pir_sc, &c->pir_dg, &c->pir_u, &c->pir_dd})
+                           &c->pir_sc, &c->pir_dg, &c->pir_u, &c->pir_dd, &c->pd_first, &c->pd_col, &c->pd_A, &c->pd_B,
+                           &c->pd_T, &c->pd_X, &c->pd_add, &c->pd_out, &c->pd_rlk})
         b->release();
     c->pir_map.release();
+    c->ext_const.release();
+    if (c->ext) wally_destroy(c->ext);
     delete c;
 }
 
@@ -1437,27 +1493,30 @@ int wally_pir_load(wally_ctx *c, uint32_t rows, uint32_t cols, const uint64_t *t
     const size_t N = c->N, L = c->L, P = (size_t)rows * cols;
     for (size_t i = 0; i < P * N; i++)
         if (table[i] >= t) return fail(WALLY_EINVAL, "table coefficient %zu is not below t", i);
-    uint32_t levels = 0;
+    uint32_t levels = 0, levels2 = 0;
     while ((1u << levels) < rows) levels++;
+    while ((1u << levels2) < rows + cols) levels2++;
+    if (levels2 > 12) levels2 = 0;  // the two-dimensional query needs rows + cols <= 4096
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     c->pir_rows = c->pir_cols = c->pir_levels = 0;
     c->pir_db.release();
     DevBuf<u64> raw;
     if (raw.ensure(P * N) != cudaSuccess || c->pir_db.ensure(P * L * N) != cudaSuccess ||
-        c->pir_mono.ensure(std::max<size_t>(levels, 1) * L * N) != cudaSuccess)
+        c->pir_mono.ensure(std::max<size_t>(std::max(levels, levels2), 1) * L * N) != cudaSuccess)
         return fail(WALLY_ENOMEM, "cannot allocate the PIR table (%.2f GB)", P * L * N * 8.0 / 1e9);
     CUDA_TRY(cudaMemcpyAsync(raw.p, table, 8 * P * N, cudaMemcpyHostToDevice, st));
     CUDA_TRY(launch_pir_lift(c->dp, raw.p, (u32)P, c->pir_db.p, st));
     CUDA_TRY(launch_to_ntt(c->dp, nullptr, c->pir_db.p, L * N, c->pir_db.p, L * N, (u32)L, (u32)L, (u32)P, nullptr,
                            true, st));
     // X^(-2^a) = -X^(N - 2^a): its NTT per limb, times 2^64
-    std::vector<uint64_t> mono(std::max<size_t>(levels, 1) * L * N, 0);
-    for (uint32_t a = 0; a < levels; a++)
+    const uint32_t lmax = std::max(levels, levels2);
+    std::vector<uint64_t> mono(std::max<size_t>(lmax, 1) * L * N, 0);
+    for (uint32_t a = 0; a < lmax; a++)
         for (size_t l = 0; l < L; l++) mono[((size_t)a * L + l) * N + (N - (1u << a))] = c->mods[l] - 1;
-    if (levels) {
+    if (lmax) {
         CUDA_TRY(cudaMemcpyAsync(c->pir_mono.p, mono.data(), 8 * mono.size(), cudaMemcpyHostToDevice, st));
-        CUDA_TRY(launch_to_ntt(c->dp, nullptr, c->pir_mono.p, L * N, c->pir_mono.p, L * N, (u32)L, (u32)L, levels,
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, c->pir_mono.p, L * N, c->pir_mono.p, L * N, (u32)L, (u32)L, lmax,
                                nullptr, true, st));
     }
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -1465,6 +1524,7 @@ int wally_pir_load(wally_ctx *c, uint32_t rows, uint32_t cols, const uint64_t *t
     c->pir_rows = rows;
     c->pir_cols = cols;
     c->pir_levels = levels;
+    c->pir_levels2 = levels2;
     return WALLY_OK;
 }
 
@@ -1479,15 +1539,9 @@ int wally_pir_answer(wally_ctx *c, uint32_t n, const uint64_t *queries, const ui
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t lv = c->pir_levels, cols = c->pir_cols, rows = c->pir_rows;
     const size_t N = c->N, L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
-    const uint32_t chunk = std::min<uint32_t>(n, 8), full = 1u << lv, half = std::max(1u, full / 2);
-    const size_t items = (size_t)chunk * half;
-    if (c->pir_E[0].ensure((size_t)chunk * full * ctw) != cudaSuccess ||
-        c->pir_E[1].ensure((size_t)chunk * full * ctw) != cudaSuccess || c->pir_S.ensure(items * ctw) != cudaSuccess ||
-        c->pir_keys.ensure((size_t)chunk * std::max(lv, 1u) * keyw) != cudaSuccess ||
-        c->pir_out.ensure((size_t)chunk * cols * ctw) != cudaSuccess || c->pir_sc.ensure(items * ctw) != cudaSuccess ||
-        c->pir_dg.ensure(items * L * N) != cudaSuccess || c->pir_u.ensure(items * 2 * (L + 1) * N) != cudaSuccess ||
-        c->pir_dd.ensure(items * (L + 1) * L * N) != cudaSuccess || c->pir_map.ensure(items) != cudaSuccess)
-        return fail(WALLY_ENOMEM, "cannot allocate the PIR scratch");
+    const uint32_t chunk = std::min<uint32_t>(n, 8), full = 1u << lv;
+    int rc0 = pir_scratch(c, chunk, lv, cols);
+    if (rc0) return rc0;
     for (uint32_t q0 = 0; q0 < n; q0 += chunk) {
         const uint32_t nq = std::min(chunk, n - q0);
         // queries and keys to NTT form (keys times 2^64)
@@ -1497,32 +1551,212 @@ int wally_pir_answer(wally_ctx *c, uint32_t n, const uint64_t *queries, const ui
             CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)q0 * lv * keyw, keyw, c->pir_keys.p, keyw,
                                    2 * (u32)(L * (L + 1)), (u32)(L + 1), nq * lv, nullptr, true, st));
         int cur = 0;
-        for (uint32_t a = 0; a < lv; a++) {
-            const u32 count = nq << a;
-            CUDA_TRY(launch_pir_qmap(c->pir_map.p, count, a, st));
-            RotArgs r;
-            memset(&r, 0, sizeof(r));
-            r.src = c->pir_E[cur].p;
-            r.src_stride = ctw;
-            r.dst = c->pir_S.p;
-            r.dst_stride = ctw;
-            r.key = c->pir_keys.p + (size_t)a * keyw;
-            r.key_stride = (size_t)lv * keyw;
-            r.key_map = c->pir_map.p;
-            r.n_max = count;
-            r.galois = (uint64_t)(N >> a) + 1;
-            r.sc = c->pir_sc.p;
-            r.dg = c->pir_dg.p;
-            r.u = c->pir_u.p;
-            r.dd = c->pir_dd.p;
-            CUDA_TRY(launch_rotate(c->dp, r, st, c->pr()));
-            CUDA_TRY(launch_pir_combine(c->dp, c->pir_E[cur].p, c->pir_S.p, c->pir_E[cur ^ 1].p,
-                                        c->pir_mono.p + (size_t)a * L * N, count, a, st));
-            cur ^= 1;
-        }
+        int rc = pir_expand(c, nq, lv, cur, st);
+        if (rc) return rc;
         CUDA_TRY(launch_pir_dim1(c->dp, c->pir_db.p, rows, cols, c->pir_E[cur].p, full, nq, c->pir_out.p, st));
         CUDA_TRY(launch_from_ntt(c->dp, c->pir_out.p, out + (size_t)q0 * cols * ctw, 2 * (u32)L, (u32)L, nq * cols,
                                  st));
+    }
+    return WALLY_OK;
+}
+
+// ---------------------------------------------------------------- MulPIR's second dimension
+namespace {
+
+uint32_t bitlen_big(const std::vector<uint64_t> &a)
+{
+    for (size_t i = a.size(); i-- > 0;)
+        if (a[i]) return (uint32_t)(64 * i + 64 - __builtin_clzll(a[i]));
+    return 0;
+}
+
+bool to_words(const std::vector<uint64_t> &a, u64 *out)
+{
+    for (int i = 0; i < XW; i++) out[i] = 0;
+    for (size_t i = 0; i < a.size(); i++) {
+        if (i >= (size_t)XW) {
+            if (a[i]) return false;
+            continue;
+        }
+        out[i] = a[i];
+    }
+    return true;
+}
+
+// The extension basis of the exact tensor: further primes = 1 mod 2N below
+// P until their product exceeds 2^(12 + log2 N) Q (twice the largest
+// coefficient of a sum of up to 4096 tensors of centred lifts), its own
+// context (transform tables) and the CRT constants.
+int build_ext(wally_ctx *c)
+{
+    if (c->ext) return WALLY_OK;
+    const uint32_t L = c->L;
+    std::vector<uint64_t> Qw{1};
+    for (uint32_t i = 0; i < L; i++) Qw = big_mul_small(Qw, c->mods[i]);
+    const uint32_t need = bitlen_big(Qw) + c->log_n + 13;
+    std::vector<uint64_t> b;
+    uint32_t bits = 0;
+    uint64_t below = c->mods[L];
+    while (bits <= need) {
+        below = prime_1mod_below(below, 2 * (uint64_t)c->N);
+        if (!below) return fail(WALLY_EINVAL, "no extension primes");
+        b.push_back(below);
+        bits += 63 - __builtin_clzll(below);
+    }
+    const uint32_t Lr = L + (uint32_t)b.size();
+    if (Lr >= WALLY_MAX_LIMBS)
+        return fail(WALLY_EINVAL, "ciphertext products need %u limbs in the extension basis (at most %d)", Lr,
+                    WALLY_MAX_LIMBS - 1);
+    ExtConst ec;
+    memset(&ec, 0, sizeof(ec));
+    ec.L = (int)L;
+    ec.Lx = (int)b.size();
+    ec.Lr = (int)Lr;
+    ec.t = c->mods[L + 1];
+    std::vector<uint64_t> Rw = Qw;
+    for (uint64_t x : b) Rw = big_mul_small(Rw, x);
+    bool ok = to_words(Qw, ec.Q) && to_words(Rw, ec.R);
+    std::vector<uint64_t> twoQ = big_mul_small(Qw, 2);
+    twoQ[0] -= 1;  // 2Q is even and its low word nonzero (Q odd)
+    ok = ok && to_words(twoQ, ec.twoQm1);
+    for (uint32_t i = 0; i < L; i++) {
+        ec.q[i] = c->mods[i];
+        ec.theta[i] = c->dp.theta[i];
+        uint64_t rem;
+        std::vector<uint64_t> qi = big_div_small(Qw, c->mods[i], &rem);
+        ok = ok && to_words(qi, ec.qw[i]);
+        for (size_t k = 0; k < b.size(); k++) ec.qdiv_b[i][k] = big_mod_small(qi, b[k]);
+    }
+    for (size_t k = 0; k < b.size(); k++) {
+        ec.b[k] = b[k];
+        ec.Q_b[k] = big_mod_small(Qw, b[k]);
+    }
+    for (uint32_t l = 0; l < Lr; l++) {
+        const uint64_t r = l < L ? c->mods[l] : b[l - L];
+        ec.r[l] = r;
+        uint64_t rem;
+        std::vector<uint64_t> rl = big_div_small(Rw, r, &rem);
+        ok = ok && to_words(rl, ec.rw[l]);
+        ec.rinv[l] = invmod_h(big_mod_small(rl, r), r);
+    }
+    if (!ok) return fail(WALLY_EINVAL, "extension basis wider than %d words", XW);
+    std::vector<uint64_t> rq(ec.r, ec.r + Lr);
+    wally_params e;
+    memset(&e, 0, sizeof(e));
+    e.log_n = c->log_n;
+    e.num_q = Lr;
+    e.q_bits = 61;
+    e.t_bits = 30;
+    e.dim = c->d;
+    e.device = c->device;
+    e.q = rq.data();
+    e.t = c->mods[L + 1];
+    wally_ctx *x = nullptr;
+    int rc = wally_setup_params(&e, &x);
+    if (rc) return rc;
+    if (c->ext_const.ensure(1) != cudaSuccess) {
+        wally_destroy(x);
+        return fail(WALLY_ENOMEM, "extension constants");
+    }
+    CUDA_TRY(cudaMemcpy(c->ext_const.p, &ec, sizeof(ec), cudaMemcpyHostToDevice));
+    c->ext = x;
+    return WALLY_OK;
+}
+
+}  // namespace
+
+int wally_keygen_relin(wally_ctx *c, uint32_t n, const int8_t *secret, const uint64_t *key_a, const int8_t *key_e,
+                       uint64_t *keys, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (n == 0) return WALLY_OK;
+    if (!secret || !key_a || !key_e || !keys) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(launch_relinkey(c->dp, secret, key_a, key_e, n, keys, (cudaStream_t)stream));
+    return WALLY_OK;
+}
+
+int wally_pir_answer2(wally_ctx *c, uint32_t n, const uint64_t *queries, const uint64_t *keys,
+                      const uint64_t *relin_keys, uint64_t *out, void *stream)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    if (!c->pir_rows) return fail(WALLY_ESTATE, "no PIR table loaded");
+    if (!c->pir_levels2) return fail(WALLY_EINVAL, "rows + columns must be at most 4096");
+    if (n == 0) return WALLY_OK;
+    if (!queries || !keys || !relin_keys || !out) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    int rc = build_ext(c);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t lv = c->pir_levels2, cols = c->pir_cols, rows = c->pir_rows;
+    const size_t N = c->N, L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
+    const uint32_t Lr = c->ext->L, full = 1u << lv;
+    const uint32_t chunk = std::min<uint32_t>(n, 8);
+    rc = pir_scratch(c, chunk, lv, cols);
+    if (rc) return rc;
+    const size_t ext_ct = (size_t)2 * Lr * N;
+    if (c->pd_first.ensure((size_t)chunk * cols * ctw) != cudaSuccess ||
+        c->pd_col.ensure((size_t)chunk * cols * ctw) != cudaSuccess ||
+        c->pd_A.ensure((size_t)chunk * cols * ext_ct) != cudaSuccess ||
+        c->pd_B.ensure((size_t)chunk * cols * ext_ct) != cudaSuccess ||
+        c->pd_T.ensure((size_t)chunk * 3 * Lr * N) != cudaSuccess || c->pd_X.ensure((size_t)chunk * ctw) != cudaSuccess ||
+        c->pd_add.ensure((size_t)chunk * ctw) != cudaSuccess || c->pd_out.ensure((size_t)chunk * ctw) != cudaSuccess ||
+        c->pd_rlk.ensure((size_t)chunk * keyw) != cudaSuccess)
+        return fail(WALLY_ENOMEM, "cannot allocate the second-dimension scratch");
+    const ExtConst *ec = c->ext_const.p;
+    for (uint32_t q0 = 0; q0 < n; q0 += chunk) {
+        const uint32_t nq = std::min(chunk, n - q0);
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, queries + (size_t)q0 * ctw, ctw, c->pir_E[0].p, ctw, 2 * (u32)L,
+                               (u32)L, nq, nullptr, false, st));
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)q0 * lv * keyw, keyw, c->pir_keys.p, keyw,
+                               2 * (u32)(L * (L + 1)), (u32)(L + 1), nq * lv, nullptr, true, st));
+        int cur = 0;
+        rc = pir_expand(c, nq, lv, cur, st);
+        if (rc) return rc;
+        // first dimension over the row indicators, then both operands of the
+        // second dimension in coefficient form: the column sums and the
+        // column indicators (indicators rows .. rows + cols - 1)
+        CUDA_TRY(launch_pir_dim1(c->dp, c->pir_db.p, rows, cols, c->pir_E[cur].p, full, nq, c->pir_out.p, st));
+        CUDA_TRY(launch_from_ntt(c->dp, c->pir_out.p, c->pd_first.p, 2 * (u32)L, (u32)L, nq * cols, st));
+        for (uint32_t q = 0; q < nq; q++)
+            CUDA_TRY(launch_from_ntt(c->dp, c->pir_E[cur].p + ((size_t)q * full + rows) * ctw,
+                                     c->pd_col.p + (size_t)q * cols * ctw, 2 * (u32)L, (u32)L, cols, st));
+        // exact tensor in the extension basis, summed over the columns
+        CUDA_TRY(launch_lift_ext(ec, c->pd_first.p, nq * cols * 2, (u32)N, c->pd_A.p, st));
+        CUDA_TRY(launch_lift_ext(ec, c->pd_col.p, nq * cols * 2, (u32)N, c->pd_B.p, st));
+        CUDA_TRY(launch_to_ntt(c->ext->dp, nullptr, c->pd_A.p, Lr * N, c->pd_A.p, Lr * N, Lr, Lr, nq * cols * 2,
+                               nullptr, false, st));
+        CUDA_TRY(launch_to_ntt(c->ext->dp, nullptr, c->pd_B.p, Lr * N, c->pd_B.p, Lr * N, Lr, Lr, nq * cols * 2,
+                               nullptr, false, st));
+        CUDA_TRY(launch_tensor_acc(ec, c->pd_A.p, c->pd_B.p, nq, cols, (u32)N, c->pd_T.p, st));
+        CUDA_TRY(launch_from_ntt(c->ext->dp, c->pd_T.p, c->pd_T.p, 3 * Lr, Lr, nq, st));
+        // one rescaling, then one relinearisation: (c0, c2) key-switched from
+        // s^2 to s (Rot with the identity automorphism) plus (0, c1)
+        CUDA_TRY(launch_scale_ext(ec, c->pd_T.p, nq, (u32)N, c->pd_X.p, c->pd_add.p, st));
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, c->pd_X.p, ctw, c->pd_X.p, ctw, 2 * (u32)L, (u32)L, nq, nullptr, false,
+                               st));
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, c->pd_add.p, ctw, c->pd_add.p, ctw, 2 * (u32)L, (u32)L, nq, nullptr,
+                               false, st));
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, relin_keys + (size_t)q0 * keyw, keyw, c->pd_rlk.p, keyw,
+                               2 * (u32)(L * (L + 1)), (u32)(L + 1), nq, nullptr, true, st));
+        RotArgs r;
+        memset(&r, 0, sizeof(r));
+        r.src = c->pd_X.p;
+        r.src_stride = ctw;
+        r.dst = c->pd_out.p;
+        r.dst_stride = ctw;
+        r.add = c->pd_add.p;
+        r.add_stride = ctw;
+        r.key = c->pd_rlk.p;
+        r.key_stride = keyw;
+        r.n_max = nq;
+        r.galois = 1;
+        r.sc = c->pir_sc.p;
+        r.dg = c->pir_dg.p;
+        r.u = c->pir_u.p;
+        r.dd = c->pir_dd.p;
+        CUDA_TRY(launch_rotate(c->dp, r, st, c->pr()));
+        CUDA_TRY(launch_from_ntt(c->dp, c->pd_out.p, out + (size_t)q0 * ctw, 2 * (u32)L, (u32)L, nq, st));
     }
     return WALLY_OK;
 }

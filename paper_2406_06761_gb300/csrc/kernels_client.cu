@@ -269,6 +269,58 @@ __global__ void NTT_LB_WIDE(LOGN) k_keygen(const DevParams *dpp, const int8_t *s
     }
 }
 
+// Relinearisation key, CTA (client n, modulus j, digit i): the key
+// switching key from s^2 to s (MulPIR's ciphertext products, Sec. 4.2):
+// b_i = -a_i*s + e_i + [i == j] P s^2 (mod q_j), b_i = -a_i*s + e_i (mod P),
+// with s^2 the negacyclic square of the secret, formed here mod p_j.
+template <int LOGN>
+__global__ void NTT_LB_WIDE(LOGN) k_relinkey(const DevParams *dpp, const int8_t *secret, const u64 *key_a,
+                                        const int8_t *key_e, u64 *keys)
+{
+    constexpr int N = 1 << LOGN, T = N / 32;
+    extern __shared__ u64 sm[];
+    Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
+    Tw *twi = twf;  // one cache, reloaded by every transform
+    __shared__ Mod md;
+    const u32 n = blockIdx.x;
+    const int j = blockIdx.y, L = dpp->L, i = blockIdx.z;
+    load_mod(&md, dpp, j);
+    const u64 p = md.p;
+    const int8_t *s = secret + (size_t)n * N;
+    u64 sv[32], s2[32];
+    secret_ntt<LOGN>(sm, sv, s, md, twf);
+#pragma unroll
+    for (int u = 0; u < 32; u++) {
+        const int v = s[threadIdx.x + T * u];
+        sm[spos(threadIdx.x + T * u)] = v < 0 ? p - 1 : (u64)v;
+    }
+    poly_times_secret<LOGN>(sm, sv, md, twf, twi);
+#pragma unroll
+    for (int u = 0; u < 32; u++) s2[u] = inv_finish(sm[spos(threadIdx.x + T * u)], md);
+    __syncthreads();
+    const u64 *a = key_a + (((size_t)n * L + i) * (L + 1) + j) * N;
+#pragma unroll 8
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        sm[spos(e)] = a[e];
+    }
+    poly_times_secret<LOGN>(sm, sv, md, twf, twi);
+    const int8_t *ee = key_e + ((size_t)n * L + i) * N;
+    u64 *kb = keys + ((((size_t)n * L + i) * 2 + 0) * (L + 1) + j) * N;
+    u64 *ka = keys + ((((size_t)n * L + i) * 2 + 1) * (L + 1) + j) * N;
+    const u64 pm = dpp->pmodq[j < L ? j : 0];
+#pragma unroll 4
+    for (int u = 0; u < 32; u++) {
+        const int e = threadIdx.x + T * u;
+        const u64 as = inv_finish(sm[spos(e)], md);
+        const int ev = ee[e];
+        u64 v = submod(ev < 0 ? p - (u64)(-ev) : (u64)ev, as, p);
+        if (i == j) v = addmod(v, mulmod(pm, s2[u], md), p);
+        kb[e] = v;
+        ka[e] = a[e];
+    }
+}
+
 // CTA (ciphertext n, limb l): x_l = [c0 + c1 s]_{q_l}, coefficient form.
 template <int LOGN>
 __global__ void NTT_LB_WIDE(LOGN) k_decrypt_residues(const DevParams *dpp, const int8_t *secret, const u32 *secret_index,
@@ -475,6 +527,7 @@ cudaError_t set_attrs_logn()
     SA(k_encode_query);
     SA(k_encrypt);
     SA(k_keygen);
+    SA(k_relinkey);
     SA(k_decrypt_residues);
     SA(k_decrypt_scale);
     SA(k_decrypt_compressed);
@@ -582,6 +635,16 @@ cudaError_t launch_decrypt(const DevParams &dp, const int8_t *secret, const u32 
                           dpp, secret, secret_index, cts, xs);
                       k_decrypt_scale<LG><<<n, ntt_threads(LG), smem_bytes(LG), st>>>(dpp, xs, scores, true);
                   }));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relinkey(const DevParams &dp, const int8_t *secret, const u64 *key_a, const int8_t *key_e, u32 n,
+                            u64 *keys, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const DevParams *dpp = device_params_of(dp);
+    DISPATCH_LOGN(dp.log_n, (k_relinkey<LG><<<dim3(n, dp.L + 1, dp.L), ntt_threads(LG), smem_bytes(LG), st>>>(
+                                dpp, secret, key_a, key_e, keys)));
     return cudaGetLastError();
 }
 

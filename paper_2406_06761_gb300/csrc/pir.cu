@@ -86,6 +86,217 @@ __global__ void __launch_bounds__(256) k_pir_dim1(const DevParams *dpp, const u6
     if (q < n) out[((size_t)q * cols + j) * ctw + (size_t)comp * L * N + (size_t)l * N + s] = mont_redc(hi, lo, dpp->m[l]);
 }
 
+// ---- multiword integers: XW little-endian 64-bit words, non-negative
+__device__ __forceinline__ void mw_zero(u64 *a)
+{
+#pragma unroll
+    for (int i = 0; i < XW; i++) a[i] = 0;
+}
+
+// a += b * m
+__device__ __forceinline__ void mw_mul_add(u64 *a, const u64 *b, u64 m)
+{
+    unsigned __int128 carry = 0;
+#pragma unroll
+    for (int i = 0; i < XW; i++) {
+        const unsigned __int128 v = (unsigned __int128)b[i] * m + a[i] + carry;
+        a[i] = (u64)v;
+        carry = v >> 64;
+    }
+}
+
+__device__ __forceinline__ int mw_cmp(const u64 *a, const u64 *b)
+{
+    for (int i = XW - 1; i >= 0; i--)
+        if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+    return 0;
+}
+
+// a -= b (a >= b)
+__device__ __forceinline__ void mw_sub(u64 *a, const u64 *b)
+{
+    u64 borrow = 0;
+#pragma unroll
+    for (int i = 0; i < XW; i++) {
+        const u64 x = a[i], y = b[i];
+        const u64 d = x - y - borrow;
+        borrow = (x < y) || (x == y && borrow) ? 1 : 0;
+        a[i] = d;
+    }
+}
+
+// a += b
+__device__ __forceinline__ void mw_add(u64 *a, const u64 *b)
+{
+    u64 carry = 0;
+#pragma unroll
+    for (int i = 0; i < XW; i++) {
+        const u64 s1 = a[i] + b[i];
+        const u64 c1 = s1 < a[i];
+        const u64 s2 = s1 + carry;
+        carry = c1 | (s2 < s1);
+        a[i] = s2;
+    }
+}
+
+// a = floor(a / d), returns a mod d
+__device__ __forceinline__ u64 mw_div_small(u64 *a, u64 d)
+{
+    unsigned __int128 rem = 0;
+    for (int i = XW - 1; i >= 0; i--) {
+        const unsigned __int128 cur = (rem << 64) | a[i];
+        a[i] = (u64)(cur / d);
+        rem = cur % d;
+    }
+    return (u64)rem;
+}
+
+__device__ __forceinline__ u64 mw_mod_small(const u64 *a, u64 d)
+{
+    unsigned __int128 rem = 0;
+    for (int i = XW - 1; i >= 0; i--) rem = ((rem << 64) | a[i]) % d;
+    return (u64)rem;
+}
+
+// 2a > b ?
+__device__ __forceinline__ bool mw_twice_gt(const u64 *a, const u64 *b)
+{
+    u64 d[XW];
+    u64 carry = 0;
+#pragma unroll
+    for (int i = 0; i < XW; i++) {
+        d[i] = (a[i] << 1) | carry;
+        carry = a[i] >> 63;
+    }
+    return carry || mw_cmp(d, b) > 0;
+}
+
+// Centred lift into the extension basis, one thread per coefficient: with
+// y_i = [x_i theta_i]_{q_i}, S = sum_i y_i Q/q_i = A + k Q exactly
+// (multiword), k chosen so that A lies in (-Q/2, Q/2]; then
+// A mod b = sum_i y_i [Q/q_i]_b - k [Q]_b.
+__global__ void k_lift_ext(const ExtConst *ec, const u64 *src, u32 count, u32 n, u64 *dst)
+{
+    const int L = ec->L, Lx = ec->Lx, Lr = ec->Lr;
+    const size_t total = (size_t)count * n;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = idx / n;
+        const u32 e = (u32)(idx % n);
+        u64 y[WALLY_MAX_LIMBS];
+        u64 S[XW];
+        mw_zero(S);
+        for (int i = 0; i < L; i++) {
+            const u64 x = src[(p * L + i) * n + e];
+            dst[(p * Lr + i) * n + e] = x;
+            y[i] = (u64)(((unsigned __int128)x * ec->theta[i]) % ec->q[i]);
+            mw_mul_add(S, ec->qw[i], y[i]);
+        }
+        u32 k = 0;
+        while (mw_cmp(S, ec->Q) >= 0) {
+            mw_sub(S, ec->Q);
+            k++;
+        }
+        if (mw_twice_gt(S, ec->Q)) k++;  // centred: A = S - Q < 0
+        for (int j = 0; j < Lx; j++) {
+            const u64 b = ec->b[j];
+            unsigned __int128 acc = (unsigned __int128)k * (b - ec->Q_b[j]);
+            for (int i = 0; i < L; i++) acc += (unsigned __int128)y[i] * ec->qdiv_b[i][j];
+            dst[(p * Lr + L + j) * n + e] = (u64)(acc % b);
+        }
+    }
+}
+
+// Thread per (query, limb, coefficient) of the extension basis: three lazy
+// 128-bit sums over the d2 pairs, reduced once.
+__global__ void k_tensor_acc(const ExtConst *ec, const u64 *A, const u64 *B, u32 nq, u32 d2, u32 n, u64 *T)
+{
+    const int Lr = ec->Lr;
+    const size_t per = (size_t)2 * Lr * n;  // one ciphertext
+    const size_t total = (size_t)nq * Lr * n;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const u32 q = (u32)(idx / ((size_t)Lr * n));
+        const size_t le = idx % ((size_t)Lr * n);  // l * n + e
+        const u64 p = ec->r[le / n];
+        u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0, h2 = 0, l2 = 0;
+        for (u32 j = 0; j < d2; j++) {
+            const size_t base = ((size_t)q * d2 + j) * per + le;
+            const u64 a0 = A[base], a1 = A[base + (size_t)Lr * n], b0 = B[base], b1 = B[base + (size_t)Lr * n];
+            mac128(h0, l0, a0, b0);
+            mac128(h1, l1, a0, b1);
+            mac128(h1, l1, a1, b0);
+            mac128(h2, l2, a1, b1);
+        }
+        const size_t o = (size_t)q * 3 * Lr * n + le;
+        T[o] = (u64)((((unsigned __int128)h0 << 64) | l0) % p);
+        T[o + (size_t)Lr * n] = (u64)((((unsigned __int128)h1 << 64) | l1) % p);
+        T[o + (size_t)2 * Lr * n] = (u64)((((unsigned __int128)h2 << 64) | l2) % p);
+    }
+}
+
+// Thread per (query, tensor component, coefficient): CRT over the extension
+// basis to the centred integer V, then round(t V / Q) = floor((2tV + Q) / 2Q)
+// by successive single-word divisions (2, q_0, ..., q_{L-1}), reduced mod q_i.
+__global__ void k_scale_ext(const ExtConst *ec, const u64 *T, u32 nq, u32 n, u64 *X, u64 *ADD)
+{
+    const int L = ec->L, Lr = ec->Lr;
+    const size_t total = (size_t)nq * 3 * n;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const u32 q = (u32)(idx / ((size_t)3 * n));
+        const int k = (int)((idx / n) % 3);
+        const u32 e = (u32)(idx % n);
+        u64 S[XW];
+        mw_zero(S);
+        for (int l = 0; l < Lr; l++) {
+            const u64 v = T[(((size_t)q * 3 + k) * Lr + l) * n + e];
+            const u64 y = (u64)(((unsigned __int128)v * ec->rinv[l]) % ec->r[l]);
+            mw_mul_add(S, ec->rw[l], y);
+        }
+        while (mw_cmp(S, ec->R) >= 0) mw_sub(S, ec->R);
+        const bool neg = mw_twice_gt(S, ec->R);
+        u64 V[XW];
+        if (neg) {
+            for (int i = 0; i < XW; i++) V[i] = ec->R[i];
+            mw_sub(V, S);  // |V| = R - S
+        } else {
+            for (int i = 0; i < XW; i++) V[i] = S[i];
+        }
+        u64 M[XW];
+        mw_zero(M);
+        mw_mul_add(M, V, 2 * ec->t);  // 2t |V|
+        bool res_neg = false, zero = false;
+        if (!neg) {
+            mw_add(M, ec->Q);  // 2tV + Q >= 0: floor division
+        } else if (mw_cmp(M, ec->Q) <= 0) {
+            zero = true;  // 0 <= Q - 2t|V| <= Q < 2Q
+        } else {
+            mw_sub(M, ec->Q);      // m = 2t|V| - Q > 0
+            mw_add(M, ec->twoQm1);  // ceil(m / 2Q) = floor((m + 2Q - 1) / 2Q)
+            res_neg = true;
+        }
+        u64 res[WALLY_MAX_LIMBS];
+        if (zero) {
+            for (int i = 0; i < L; i++) res[i] = 0;
+        } else {
+            mw_div_small(M, 2);
+            for (int i = 0; i < L; i++) mw_div_small(M, ec->q[i]);
+            for (int i = 0; i < L; i++) {
+                const u64 r = mw_mod_small(M, ec->q[i]);
+                res[i] = (res_neg && r) ? ec->q[i] - r : r;
+            }
+        }
+        // k = 0 -> c0 (X comp 0), k = 2 -> c2 (X comp 1), k = 1 -> c1 (ADD comp 1)
+        for (int i = 0; i < L; i++) {
+            const size_t o = ((size_t)q * 2 * L + i) * n + e;
+            if (k == 0) X[o] = res[i];
+            else if (k == 2) X[o + (size_t)L * n] = res[i];
+            else {
+                ADD[o] = 0;
+                ADD[o + (size_t)L * n] = res[i];
+            }
+        }
+    }
+}
+
 unsigned grid_for(size_t total)
 {
     size_t b = (total + 255) / 256;
@@ -113,6 +324,28 @@ cudaError_t launch_pir_combine(const DevParams &dp, const u64 *cur, const u64 *s
 {
     if (!count) return cudaSuccess;
     k_pir_combine<<<grid_for((size_t)count * 2 * dp.L * dp.n), 256, 0, st>>>(dp.self, cur, sig, next, mono, count, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lift_ext(const ExtConst *ec, const u64 *src, u32 count, u32 n, u64 *dst, cudaStream_t st)
+{
+    if (!count) return cudaSuccess;
+    k_lift_ext<<<grid_for((size_t)count * n), 256, 0, st>>>(ec, src, count, n, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tensor_acc(const ExtConst *ec, const u64 *A, const u64 *B, u32 nq, u32 d2, u32 n, u64 *T,
+                              cudaStream_t st)
+{
+    if (!nq) return cudaSuccess;
+    k_tensor_acc<<<grid_for((size_t)nq * WALLY_MAX_LIMBS * n), 256, 0, st>>>(ec, A, B, nq, d2, n, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_ext(const ExtConst *ec, const u64 *T, u32 nq, u32 n, u64 *X, u64 *ADD, cudaStream_t st)
+{
+    if (!nq) return cudaSuccess;
+    k_scale_ext<<<grid_for((size_t)nq * 3 * n), 256, 0, st>>>(ec, T, nq, n, X, ADD);
     return cudaGetLastError();
 }
 

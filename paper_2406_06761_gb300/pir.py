@@ -9,11 +9,12 @@ Fetch"): host-side tables and client logic around the library's index PIR.
   ("uneven dimensions": d2 = sqrt(1/(gamma + 1)) sqrt(N') with gamma = 5).
 - A slot's plaintext packs the keyword, the value length and the value, two
   bytes a coefficient; empty slots are zero (keyword 0 is reserved).
-- The client sends, per table, a query ciphertext for the slot's row and one
-  set of expansion keys (the same Galois elements N/2^a + 1 serve both
-  tables); the server answers with the slot's whole row (wally_pir_answer);
-  the client decrypts the slot's column and keeps the entry whose keyword
-  matches.
+- The client sends, per table, a query ciphertext for the slot's row (and
+  column) and one set of expansion keys (the same Galois elements N/2^a + 1
+  serve both tables); the server answers with the slot's whole row
+  (wally_pir_answer, MulPIR's first dimension) or with the slot alone
+  (wally_pir_answer2, both dimensions, which also needs a relinearisation
+  key); the client decrypts and keeps the entry whose keyword matches.
 
 Every homomorphic step runs in libwally; this module only builds tables and
 packs bytes.
@@ -108,7 +109,8 @@ def build(entries: dict[int, bytes], load: float = 2.2, max_kicks: int = 500, se
     if any(k <= 0 or k > _MASK for k in entries):
         raise ValueError("keywords must be in 1 .. 2^64 - 1")
     n = len(entries)
-    size = max(1, math.ceil(load * n / 2))
+    milli = int(round(load * 1000))
+    size = max(1, -(-milli * n // 2000))  # ceil(load n / 2) without floating error
     for attempt in range(tries):
         sd = seed + attempt
         tabs = [[None] * size, [None] * size]

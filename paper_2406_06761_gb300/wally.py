@@ -94,6 +94,8 @@ SIGNATURES = {
     "wally_pir_load": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp]),
     "wally_pir_answer": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp]),
     "wally_keygen_galois": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "wally_pir_answer2": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
+    "wally_keygen_relin": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "wally_encrypt_poly": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "wally_decrypt_poly": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "wally_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(wally_tuning)]),
@@ -302,6 +304,17 @@ def wally_pir_load(ctx: int, table, stream=None) -> None:
 def wally_pir_answer(ctx: int, n: int, queries, keys, out, stream=None) -> None:
     _require_cuda(queries, keys, out)
     _check(load().wally_pir_answer(ctx, n, _ptr(queries), _ptr(keys), _ptr(out), _stream(stream)))
+
+
+def wally_pir_answer2(ctx: int, n: int, queries, keys, relin_keys, out, stream=None) -> None:
+    _require_cuda(queries, keys, relin_keys, out)
+    _check(load().wally_pir_answer2(ctx, n, _ptr(queries), _ptr(keys), _ptr(relin_keys), _ptr(out),
+                                    _stream(stream)))
+
+
+def wally_keygen_relin(ctx: int, n: int, secret, key_a, key_e, keys, stream=None) -> None:
+    _require_cuda(secret, key_a, key_e, keys)
+    _check(load().wally_keygen_relin(ctx, n, _ptr(secret), _ptr(key_a), _ptr(key_e), _ptr(keys), _stream(stream)))
 
 
 def wally_keygen_galois(ctx: int, n: int, galois, secret, key_a, key_e, keys, stream=None) -> None:

@@ -1,7 +1,9 @@
 """Index PIR (the server side of Sec. 4.2's keyword PIR) on the GPU against
-the oracle, bit for bit: Galois keys for the expansion elements, encryption
-and decryption of coefficient plaintexts, and the answer (oblivious
-expansion + MulPIR's first dimension)."""
+the oracle, bit for bit: Galois keys for the expansion elements,
+relinearisation keys, encryption and decryption of coefficient plaintexts,
+the one-dimensional answer (oblivious expansion + MulPIR's first dimension)
+and the two-dimensional one (+ the second dimension by ciphertext
+products)."""
 import numpy as np
 import pytest
 import torch
@@ -122,4 +124,57 @@ def test_pir_errors():
     with pytest.raises(Wl.WallyError) as e:
         Wl.wally_pir_load(ctx.ptr, bad)
     assert e.value.code == Wl.WALLY_EINVAL
+    ctx.close()
+
+
+def test_relin_key_parity():
+    prm, ctx = _setup("tiny")
+    cr = W.client_randomness(2, prm.N, prm.q, prm.P, seed=71)
+    keys = torch.empty((2, prm.L, 2, prm.L + 1, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_keygen_relin(ctx.ptr, 2, torch.from_numpy(cr.secret).to(DEV), Wl.u64_tensor(cr.key_a[:, 0], DEV),
+                          torch.from_numpy(np.ascontiguousarray(cr.key_e[:, 0])).to(DEV), keys)
+    got = Wl.to_u64_numpy(keys)
+    for i in range(2):
+        assert np.array_equal(got[i], O.relin_keygen(prm, cr.secret[i], cr.key_a[i, 0], cr.key_e[i, 0])), i
+    ctx.close()
+
+
+@pytest.mark.parametrize("rows,cols,nq", [(4, 2, 3), (40, 9, 10)])
+def test_pir_two_dimensions(rows, cols, nq):
+    """MulPIR with both dimensions at N = 8192, three 50-bit limbs: one
+    answer ciphertext a query, decrypting to table[row][col]; the first
+    query bit for bit against the oracle (expansion, first dimension, exact
+    tensor summed over the columns, one rescaling, one relinearisation)."""
+    prm, ctx = _setup("batched")
+    levels = (rows + cols - 1).bit_length()
+    db = W.pir_plaintexts(rows, cols, prm.N, prm.t, seed=72)
+    Wl.wally_pir_load(ctx.ptr, db)
+    rng = np.random.default_rng(73)
+    want = [(int(rng.integers(0, rows)), int(rng.integers(0, cols))) for _ in range(nq)]
+    cr = W.pir_client_randomness(nq, levels, prm.N, prm.q, prm.P, seed=74)
+    rc = W.client_randomness(nq, prm.N, prm.q, prm.P, seed=75)
+    sec = torch.from_numpy(cr.secret).to(DEV)
+    keys = torch.empty((nq, levels, prm.L, 2, prm.L + 1, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_keygen_galois(ctx.ptr, nq, [O.pir_galois(prm, a) for a in range(levels)], sec,
+                           Wl.u64_tensor(cr.key_a, DEV), torch.from_numpy(cr.key_e).to(DEV), keys)
+    rlk = torch.empty((nq, prm.L, 2, prm.L + 1, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_keygen_relin(ctx.ptr, nq, sec, Wl.u64_tensor(np.ascontiguousarray(rc.key_a[:, 0]), DEV),
+                          torch.from_numpy(np.ascontiguousarray(rc.key_e[:, 0])).to(DEV), rlk)
+    m = np.stack([O.pir_query_plaintext2(prm, r, c, rows, levels) for r, c in want])
+    cts = torch.empty((nq, 2, prm.L, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_encrypt_poly(ctx.ptr, nq, sec, Wl.u64_tensor(m, DEV), Wl.u64_tensor(cr.enc_a, DEV),
+                          torch.from_numpy(cr.enc_e).to(DEV), cts)
+    out = torch.empty((nq, 2, prm.L, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_pir_answer2(ctx.ptr, nq, cts, keys, rlk, out)
+    Wl.wally_sync(ctx.ptr)
+    coeffs = torch.empty((nq, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_decrypt_poly(ctx.ptr, nq, sec, None, out, coeffs)
+    dec = coeffs.cpu().numpy()
+    for i, (r, c) in enumerate(want):
+        assert np.array_equal(dec[i], db[r, c].astype(np.int64)), i
+    kg = Wl.to_u64_numpy(keys[0])
+    ind = O.pir_expand(prm, Wl.to_u64_numpy(cts[0]), [kg[a] for a in range(levels)], levels)
+    first = O.pir_first_dimension(prm, db, ind[:rows])
+    ref = O.pir_second_dimension(prm, first, ind[rows:rows + cols], Wl.to_u64_numpy(rlk[0]))
+    assert np.array_equal(Wl.to_u64_numpy(out[0]), ref)
     ctx.close()

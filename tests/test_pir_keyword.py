@@ -111,3 +111,56 @@ def test_keyword_lookup_on_the_gpu():
         assert found[i] == ent.get(k), i
     for ctx in servers:
         ctx.close()
+
+
+@pytest.mark.gpu
+def test_keyword_lookup_two_dimensions_on_the_gpu():
+    """The same lookup with MulPIR's two dimensions at N = 8192, three 50-bit
+    limbs: 100 entries, tables of 110 slots (22 x 5, 5 expansion levels for
+    rows + columns), one answer ciphertext per table and keyword."""
+    from paper_2406_06761_gb300 import wally as Wl
+    dev = torch.device("cuda", 0)
+    w = W.WORKLOADS["batched"]
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    ent = _entries(100, 5)
+    tab = pir.build(ent)
+    assert tab.dims[0] == (22, 5)
+    servers = []
+    for t in (0, 1):
+        ctx = Wl.Context(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+        Wl.wally_pir_load(ctx.ptr, tab.plaintexts(t, prm.N))
+        servers.append(ctx)
+    d1, d2 = tab.dims[0]
+    lv = (d1 + d2 - 1).bit_length()
+    keys_list = list(ent)
+    wanted = [keys_list[i] for i in (0, 42, 99)] + [777]
+    n = len(wanted)
+    cr = W.pir_client_randomness(n, lv, prm.N, prm.q, prm.P, seed=6)
+    rc = W.client_randomness(n, prm.N, prm.q, prm.P, seed=7)
+    sec = torch.from_numpy(cr.secret).to(dev)
+    ctx0 = servers[0]
+    keys = torch.empty((n, lv, prm.L, 2, prm.L + 1, prm.N), dtype=torch.int64, device=dev)
+    Wl.wally_keygen_galois(ctx0.ptr, n, [O.pir_galois(prm, a) for a in range(lv)], sec,
+                           Wl.u64_tensor(cr.key_a, dev), torch.from_numpy(cr.key_e).to(dev), keys)
+    rlk = torch.empty((n, prm.L, 2, prm.L + 1, prm.N), dtype=torch.int64, device=dev)
+    Wl.wally_keygen_relin(ctx0.ptr, n, sec, Wl.u64_tensor(np.ascontiguousarray(rc.key_a[:, 0]), dev),
+                          torch.from_numpy(np.ascontiguousarray(rc.key_e[:, 0])).to(dev), rlk)
+    found = [None] * n
+    for t in (0, 1):
+        m = np.stack([O.pir_query_plaintext2(prm, *tab.position(k, t), d1, lv) for k in wanted])
+        cts = torch.empty((n, 2, prm.L, prm.N), dtype=torch.int64, device=dev)
+        Wl.wally_encrypt_poly(ctx0.ptr, n, sec, Wl.u64_tensor(m, dev), Wl.u64_tensor(cr.enc_a, dev),
+                              torch.from_numpy(cr.enc_e).to(dev), cts)
+        out = torch.empty((n, 2, prm.L, prm.N), dtype=torch.int64, device=dev)
+        Wl.wally_pir_answer2(servers[t].ptr, n, cts, keys, rlk, out)
+        Wl.wally_sync(servers[t].ptr)
+        coeffs = torch.empty((n, prm.N), dtype=torch.int64, device=dev)
+        Wl.wally_decrypt_poly(ctx0.ptr, n, sec, None, out, coeffs)
+        for i, row in enumerate(coeffs.cpu().numpy()):
+            e = pir.unpack(row)
+            if e is not None and e[0] == wanted[i]:
+                found[i] = e[1]
+    for i, k in enumerate(wanted):
+        assert found[i] == ent.get(k), i
+    for ctx in servers:
+        ctx.close()

@@ -1538,7 +1538,7 @@ int wally_pir_answer(wally_ctx *c, uint32_t n, const uint64_t *queries, const ui
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t lv = c->pir_levels, cols = c->pir_cols, rows = c->pir_rows;
-    const size_t N = c->N, L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
+    const size_t L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
     const uint32_t chunk = std::min<uint32_t>(n, 8), full = 1u << lv;
     int rc0 = pir_scratch(c, chunk, lv, cols);
     if (rc0) return rc0;

@@ -20,13 +20,6 @@ __device__ __forceinline__ void load_mod(Mod *s, const DevParams *dpp, int j)
     __syncthreads();
 }
 
-__device__ __forceinline__ u32 item_count(u32 n_max, const u32 *n_dev)
-{
-    if (!n_dev) return n_max;
-    u32 c = *n_dev;
-    return c < n_max ? c : n_max;
-}
-
 #define NTT_LB(LOGN) __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::MIN_BLOCKS)
 #define NTT_LB_WIDE(LOGN) __launch_bounds__(NttShape<LOGN>::T)
 
@@ -362,7 +355,6 @@ __global__ void NTT_LB_WIDE(LOGN) k_decrypt_scale(const DevParams *dpp, const u6
     constexpr int N = 1 << LOGN, T = N / 32;
     extern __shared__ u64 sm[];
     Tw *twf = reinterpret_cast<Tw *>(sm + smem_words(1 << LOGN));
-    Tw *twi = twf;  // one cache, reloaded by every transform
     __shared__ Mod md;
     const u32 n = blockIdx.x;
     const int L = dpp->L;

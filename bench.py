@@ -105,9 +105,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(kernel: str):
+def recorded_traffic(kernel: str, items_per_launch: float | None = None):
     """DRAM bytes per launch of `kernel` from the committed ncu summary in
-    profiles/, or None when that capture was taken on other kernel sources."""
+    profiles/ (a launch of 1,024 items), scaled to `items_per_launch` items
+    (the key-switch kernels' traffic grows in proportion to the items), or
+    None when that capture was taken on other kernel sources."""
     path = os.path.join(ROOT, "profiles", f"ncu_{kernel}_1024_items.md")
     if not os.path.exists(path):
         return None
@@ -119,9 +121,10 @@ def recorded_traffic(kernel: str):
     if fields.get("kernel_source_sha256") != kernel_source_hash():
         return None
     try:
-        return float(fields["dram_bytes_per_launch"])
+        b = float(fields["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+    return b if items_per_launch is None else b / 1024.0 * items_per_launch
 
 
 # ---------------------------------------------------------------- algorithmic work
@@ -253,11 +256,15 @@ def main():
     ap.add_argument("--real-queries", type=int, default=None, help="override the batch size (testing)")
     ap.add_argument("--serving", action="store_true", help="measure the serving loop instead of the batch")
     ap.add_argument("--serving-seconds", type=float, default=10.0)
+    ap.add_argument("--pir", action="store_true", help="measure the metadata fetch (keyword PIR) instead")
+    ap.add_argument("--pir-clients", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.serving:
         return run_serving(args)
+    if args.pir:
+        return run_pir(args)
 
     import numpy as np
     import torch
@@ -375,7 +382,9 @@ def main():
         achieved = work[dom] / (kern[dom]["share"] * ms_step * args.steps / 1e3)
         peak = peaks["mac128_per_s"] if dom == "mac" else peaks["butterfly_per_s"]
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": "Gmodmul/s", "frac": achieved / peak, "traffic": recorded_traffic(dom),
+                "unit": "Gmodmul/s", "frac": achieved / peak, "traffic": recorded_traffic(dom, ks_count / max(1, kern[dom]["launches"]) if dom.startswith("ks_") else None),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1,024-item launch "
+                                  "(profiles/), scaled to this run's mean items per launch",
                 "peak_source": "measured: wally_measure_int_peaks (" +
                                ("128-bit multiply-accumulate" if dom == "mac" else "NTT butterfly") +
                                " throughput, all SMs, this GPU)",
@@ -496,6 +505,90 @@ def run_serving(args):
                        "batch_capacity_qps": capacity},
             "serving": results}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_pir(args):
+    """The metadata fetch of Sec. 4.2: keyword PIR over one cluster's
+    metadata (the full-scale database's mean cluster: 1,778 entries of 1 KB),
+    split cuckoo tables, MulPIR with both dimensions at N = 8192, three
+    50-bit limbs.  A lookup is two index PIR answers (one per table);
+    reports lookups/s for a batch of clients with device-resident queries
+    and keys, and checks the first lookups by decryption."""
+    import numpy as np
+    import torch
+    from paper_2406_06761_gb300 import pir
+    from paper_2406_06761_gb300 import wally as Wl
+    from paper_2406_06761_gb300 import workload as W
+    dev = torch.device("cuda", 0)
+    w = W.WORKLOADS["batched"]
+    rng = np.random.default_rng(11)
+    entries = {}
+    while len(entries) < 1778:
+        entries[int(rng.integers(1, 2**63))] = bytes(rng.integers(0, 256, 1024, dtype=np.uint8))
+    tab = pir.build(entries)
+    (d1, d2) = tab.dims[0]
+    servers = []
+    for t in (0, 1):
+        ctx = Wl.Context(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+        Wl.wally_pir_load(ctx.ptr, tab.plaintexts(t, ctx.N))
+        servers.append(ctx)
+    ctx0 = servers[0]
+    N, L, q, P, tval = ctx0.N, ctx0.L, ctx0.q, ctx0.P, int(ctx0.info.t)
+    n = args.pir_clients
+    lv = (d1 + d2 - 1).bit_length()
+    keys_list = list(entries)
+    wanted = [keys_list[int(i)] for i in rng.integers(0, len(keys_list), n)]
+    cr = W.pir_client_randomness(n, lv, N, q, P, seed=12)
+    rc = W.client_randomness(n, N, q, P, seed=13)
+    sec = torch.from_numpy(cr.secret).to(dev)
+    keys = torch.empty((n, lv, L, 2, L + 1, N), dtype=torch.int64, device=dev)
+    Wl.wally_keygen_galois(ctx0.ptr, n, pir.galois_elements(N, lv), sec,
+                           Wl.u64_tensor(cr.key_a, dev), torch.from_numpy(cr.key_e).to(dev), keys)
+    rlk = torch.empty((n, L, 2, L + 1, N), dtype=torch.int64, device=dev)
+    Wl.wally_keygen_relin(ctx0.ptr, n, sec, Wl.u64_tensor(np.ascontiguousarray(rc.key_a[:, 0]), dev),
+                          torch.from_numpy(np.ascontiguousarray(rc.key_e[:, 0])).to(dev), rlk)
+    cts, outs = [], []
+    for t in (0, 1):
+        m = np.stack([pir.query_plaintext(N, tval, lv, *tab.position(k, t), d1=d1) for k in wanted])
+        ct = torch.empty((n, 2, L, N), dtype=torch.int64, device=dev)
+        Wl.wally_encrypt_poly(ctx0.ptr, n, sec, Wl.u64_tensor(m, dev), Wl.u64_tensor(cr.enc_a, dev),
+                              torch.from_numpy(cr.enc_e).to(dev), ct)
+        cts.append(ct)
+        outs.append(torch.empty((n, 2, L, N), dtype=torch.int64, device=dev))
+
+    def step():
+        for t in (0, 1):
+            Wl.wally_pir_answer2(servers[t].ptr, n, cts[t], keys, rlk, outs[t])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(args.steps):
+        step()
+    s1.record()
+    torch.cuda.synchronize(dev)
+    ms = s0.elapsed_time(s1) / args.steps
+    ok = 0
+    for t in (0, 1):
+        coeffs = torch.empty((n, N), dtype=torch.int64, device=dev)
+        Wl.wally_decrypt_poly(ctx0.ptr, n, sec, None, outs[t], coeffs)
+        for i, row in enumerate(coeffs.cpu().numpy()):
+            e = pir.unpack(row)
+            if e is not None and e[0] == wanted[i] and e[1] == entries[wanted[i]]:
+                ok += 1
+    line = {"metric": "metadata fetch: keyword PIR lookups/s (split cuckoo tables, MulPIR, both dimensions)",
+            "value": n / (ms / 1e3), "unit": "lookups/s", "n_gpus": 1, "higher_is_better": True,
+            "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "metadata of one cluster", "entries": len(entries), "value_bytes": 1024,
+                       "table_slots": tab.sizes[0], "d1": d1, "d2": d2, "expansion_levels": lv, "clients": n,
+                       "N": N, "L": L},
+            "checked_lookups": {"found": ok, "of": n}}
+    print(json.dumps(line), flush=True)
+    for ctx in servers:
+        ctx.close()
     return 0
 
 

@@ -273,9 +273,9 @@ int wally_pir_load(wally_ctx *ctx, uint32_t rows, uint32_t cols, const uint64_t 
  *   queries  uint64_t [n][2][L][N]                 the clients' query ciphertexts
  *   keys     uint64_t [n][c][L][2][L+1][N]         per query, the key of N/2^a + 1 for level a < c
  *   out      uint64_t [n][cols][2][L][N]           column j of query q: table[row_q][j]
- * Asynchronous on `stream`; works on up to 8 queries at a time in scratch the
- * context owns (about 5 * 2^c ciphertexts a query at L = 3, plus its keys and
- * answer).
+ * Asynchronous on `stream`; works on up to 64 queries at a time in scratch
+ * the context owns (about 5 * 2^c ciphertexts a query at L = 3, plus its keys
+ * and answer).
  * Errors: WALLY_ESTATE (no table), WALLY_EINVAL, WALLY_ENOMEM, WALLY_ECUDA. */
 int wally_pir_answer(wally_ctx *ctx, uint32_t n, const uint64_t *queries, const uint64_t *keys, uint64_t *out,
                      void *stream);

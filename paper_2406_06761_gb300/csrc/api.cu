@@ -1539,7 +1539,7 @@ int wally_pir_answer(wally_ctx *c, uint32_t n, const uint64_t *queries, const ui
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t lv = c->pir_levels, cols = c->pir_cols, rows = c->pir_rows;
     const size_t L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
-    const uint32_t chunk = std::min<uint32_t>(n, 8), full = 1u << lv;
+    const uint32_t chunk = std::min<uint32_t>(n, 64), full = 1u << lv;
     int rc0 = pir_scratch(c, chunk, lv, cols);
     if (rc0) return rc0;
     for (uint32_t q0 = 0; q0 < n; q0 += chunk) {
@@ -1691,7 +1691,7 @@ int wally_pir_answer2(wally_ctx *c, uint32_t n, const uint64_t *queries, const u
     const uint32_t lv = c->pir_levels2, cols = c->pir_cols, rows = c->pir_rows;
     const size_t N = c->N, L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
     const uint32_t Lr = c->ext->L, full = 1u << lv;
-    const uint32_t chunk = std::min<uint32_t>(n, 8);
+    const uint32_t chunk = std::min<uint32_t>(n, 64);
     rc = pir_scratch(c, chunk, lv, cols);
     if (rc) return rc;
     const size_t ext_ct = (size_t)2 * Lr * N;

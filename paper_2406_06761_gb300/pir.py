@@ -143,3 +143,19 @@ def lookup_plain(tables: CuckooTables, keyword: int) -> bytes | None:
 def levels(d1: int) -> int:
     """Expansion levels of a table with d1 rows: ceil(log2 d1)."""
     return max(0, (d1 - 1).bit_length())
+
+
+def galois_elements(n: int, levels: int) -> list[int]:
+    """The substitution elements of the expansion levels: N/2^a + 1."""
+    return [n // (1 << a) + 1 for a in range(levels)]
+
+
+def query_plaintext(n: int, t: int, levels: int, row: int, col: int | None = None, d1: int = 0) -> np.ndarray:
+    """The client's query plaintext: (2^levels)^-1 mod t at X^row, and for a
+    two-dimensional query also at X^(d1 + col)."""
+    m = np.zeros(n, np.uint64)
+    inv = pow(1 << levels, -1, t)
+    m[row] = inv
+    if col is not None:
+        m[d1 + col] = (int(m[d1 + col]) + inv) % t
+    return m

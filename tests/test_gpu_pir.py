@@ -88,14 +88,14 @@ def test_pir_answer_matches_oracle(rows, cols, wanted):
 
 
 def test_pir_answer_batched_parameters():
-    """N = 8192, three 50-bit limbs: a 64 x 4 table (6 levels), 11 queries
-    (two chunks of the answer loop); all decrypt to their rows, one bit for
-    bit against the oracle."""
+    """N = 8192, three 50-bit limbs: a 64 x 4 table (6 levels), 70 queries
+    (two chunks of the answer loop, which takes 64 at a time); all decrypt
+    to their rows, one of the second chunk bit for bit against the oracle."""
     prm, ctx = _setup("batched")
     rows, cols, levels = 64, 4, 6
     db = W.pir_plaintexts(rows, cols, prm.N, prm.t, seed=54)
     Wl.wally_pir_load(ctx.ptr, db)
-    wanted = [int(x) for x in np.random.default_rng(55).integers(0, rows, 11)]
+    wanted = [int(x) for x in np.random.default_rng(55).integers(0, rows, 70)]
     cr, sec, keys, cts, _ = _client(ctx, prm, len(wanted), levels, wanted, seed=56)
     out = torch.empty((len(wanted), cols, 2, prm.L, prm.N), dtype=torch.int64, device=DEV)
     Wl.wally_pir_answer(ctx.ptr, len(wanted), cts, keys, out)
@@ -107,7 +107,7 @@ def test_pir_answer_batched_parameters():
     dec = coeffs.cpu().numpy().reshape(n, cols, prm.N)
     for i, r in enumerate(wanted):
         assert np.array_equal(dec[i], db[r].astype(np.int64)), i
-    i = 9
+    i = 67
     kg = Wl.to_u64_numpy(keys[i])
     ind = O.pir_expand(prm, Wl.to_u64_numpy(cts[i]), [kg[a] for a in range(levels)], levels)
     assert np.array_equal(Wl.to_u64_numpy(out[i]), O.pir_first_dimension(prm, db, ind))

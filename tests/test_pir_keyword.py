@@ -164,3 +164,10 @@ def test_keyword_lookup_two_dimensions_on_the_gpu():
         assert found[i] == ent.get(k), i
     for ctx in servers:
         ctx.close()
+
+
+def test_client_query_helpers_match_the_oracle(tiny_params):
+    prm = tiny_params
+    assert pir.galois_elements(prm.N, 5) == [O.pir_galois(prm, a) for a in range(5)]
+    assert np.array_equal(pir.query_plaintext(prm.N, prm.t, 4, 9), O.pir_query_plaintext(prm, 9, 4))
+    assert np.array_equal(pir.query_plaintext(prm.N, prm.t, 5, 3, 2, d1=20), O.pir_query_plaintext2(prm, 3, 2, 20, 5))

@@ -494,7 +494,12 @@ def run_serving(args):
                               ("0.9x_capacity", 0.9 * capacity, args.serving_seconds),
                               ("nominal_50k", w.arrival_qps, min(2.0, args.serving_seconds))):
         st = S.poisson_stream(rate, secs, wl.sizes, wl.pool_size, fake_fraction, seed=1)
+        Wl.wally_profile_enable(wl.ctx.ptr, True)
         r = srv.run(st)
+        prof = Wl.wally_profile_read(wl.ctx.ptr)
+        Wl.wally_profile_enable(wl.ctx.ptr, False)
+        tot = max(1e-9, sum(v[1] for v in prof.values()))
+        r["kernel_share"] = {k: round(v[1] / tot, 3) for k, v in prof.items()}
         r["offered_rate_qps"] = rate
         results[label] = r
         log(label, {k: (round(v, 2) if isinstance(v, float) else v) for k, v in r.items()})

@@ -297,7 +297,7 @@ __global__ void NTT_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
 // with 128-bit lazy accumulation and one Montgomery reduction per output
 // (plaintexts are stored times 2^64, Sec. 7 lazy reduction).
 template <int G, int CPT>
-__global__ void __launch_bounds__(256) k_mac(const DevParams *dpp, ClusterStore cs, WavePlan wp, const u64 *ctp,
+__global__ void __launch_bounds__(256, 2) k_mac(const DevParams *dpp, ClusterStore cs, WavePlan wp, const u64 *ctp,
                                              u64 *Tout, u32 m_max)
 {
     extern __shared__ u64 sm[];
@@ -332,7 +332,12 @@ __global__ void __launch_bounds__(256) k_mac(const DevParams *dpp, ClusterStore 
         __syncthreads();
         const int s = tile * ts + slot_in;
         const u32 sb = wp.seg_begin[seg], se = wp.seg_end[seg];
-        for (u32 pos = sb + ql; pos < se; pos += QL) {
+        // a segment with fewer queries than query lanes also spreads the
+        // giant-step rows i over the idle lanes (IG row groups)
+        int IG = 1;
+        while (IG * 2 <= QL && IG * 2 <= h && (u32)(QL / (IG * 2)) >= se - sb) IG *= 2;
+        const int QLp = QL / IG, qlane = ql % QLp, ig = ql / QLp;
+        for (u32 pos = sb + qlane; pos < se; pos += QLp) {
             const u64 *cq = ctp + (size_t)pos * G * ctw + (size_t)l * N + s;
             u64 cb[G][CPT];
 #pragma unroll
@@ -341,7 +346,7 @@ __global__ void __launch_bounds__(256) k_mac(const DevParams *dpp, ClusterStore 
                 for (int c = 0; c < CPT; c++) cb[b][c] = cq[(size_t)b * ctw + (size_t)(c + comp) * L * N];
             const u32 p = wp.pair_off[pos] + k;
             u64 *to = Tout + (size_t)p * h * ctw + (size_t)l * N + s;
-            for (int i = 0; i < h; i++) {
+            for (int i = ig; i < h; i += IG) {
                 u64 hi[CPT], lo[CPT];
 #pragma unroll
                 for (int c = 0; c < CPT; c++) hi[c] = lo[c] = 0;

@@ -438,6 +438,11 @@ def main():
         del out, batches
         torch.cuda.empty_cache()
         e2e = run_e2e(wl, subs, args, dev)
+        if world > 1:
+            # whole job: every rank's batch over the slowest rank's time
+            dt = M.max_over_ranks(e2e["seconds"], device=dev)
+            e2e.update(value=world * n / dt, seconds=dt, h2d_bytes_per_step=world * e2e["h2d_bytes_per_step"],
+                       d2h_bytes_per_step=world * e2e["d2h_bytes_per_step"])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -652,12 +657,15 @@ def run_e2e(wl, subs, args, dev):
     def one():
         for ids, idx, offs, ch in prepared:
             Wl.wally_eval_batch_host(wl.ctx.ptr, ids.numel(), ids, cts_h, keys_h, idx, offs, out_h[:ch])
+    from paper_2406_06761_gb300 import multigpu as M
     one()  # warm-up (pins, staging buffers)
     torch.cuda.synchronize(dev)
+    M.barrier()
     t0 = time.perf_counter()
     one()
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
+    M.barrier()
     return {"value": wl.n / dt, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "calls": len(prepared), "seconds": dt}
 

@@ -476,18 +476,36 @@ def monomial_shift(prm: Params, ct, e: int) -> np.ndarray:
     return out
 
 
-def pir_expand(prm: Params, ct, keys, levels: int) -> np.ndarray:
+def pir_key_base(prm: Params, levels: int) -> int:
+    """Sec. 4.2 "Reducing evaluation key size": (N/2^a + 1)^2 = N/2^(a-1) + 1
+    (mod 2N) while a <= floor((log2 N - 1) / 2), so the client sends the key
+    of level b = min(levels - 1, floor((log2 N - 1) / 2)) and those above it;
+    the server reaches a level a < b by substituting 2^(b - a) times with the
+    key of level b."""
+    return max(0, min(levels - 1, (prm.log_n - 1) // 2))
+
+
+def pir_expand(prm: Params, ct, keys, levels: int, derive: bool = False) -> np.ndarray:
     """Oblivious expansion (Angel et al., used by MulPIR): at level a every
     ciphertext C becomes C + sigma(C) (kept at index i) and
     (C - sigma(C)) X^(-2^a) (index i + 2^a), sigma = substitution by
-    N/2^a + 1 with keys[a].  Returns [2^levels][2][L][N]."""
+    N/2^a + 1 with keys[a].  With derive, keys holds the keys of levels
+    b .. levels - 1 only (pir_key_base) and sigma for a < b is the
+    substitution by N/2^b + 1 applied 2^(b - a) times.  Returns
+    [2^levels][2][L][N]."""
+    b = pir_key_base(prm, levels) if derive else 0
     cur = [_u64(ct)]
     for a in range(levels):
         k = pir_galois(prm, a)
         half = len(cur)
         nxt = [None] * (2 * half)
         for i, C in enumerate(cur):
-            S = rotate(prm, k, keys[a], C)
+            if derive and a < b:
+                S = C
+                for _ in range(1 << (b - a)):
+                    S = rotate(prm, pir_galois(prm, b), keys[0], S)
+            else:
+                S = rotate(prm, k, keys[a - b], C)
             nxt[i] = _ct_add(prm, C, S, +1)
             nxt[i + half] = monomial_shift(prm, _ct_add(prm, C, S, -1), 1 << a)
         cur = nxt

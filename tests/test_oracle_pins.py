@@ -695,3 +695,26 @@ def test_pir_two_dimensions_batched_params():
     ans = O.pir_second_dimension(prm, first, ind[d1:d1 + d2], rlk)
     m, _ = O.decrypt_poly(prm, cr.secret[0], ans)
     assert np.array_equal(np.asarray(m, np.uint64), db[row, col])
+
+
+def test_pir_key_derivation_by_squaring(tiny_params):
+    """Sec. 4.2 "Reducing evaluation key size": the squaring relation of the
+    substitution elements holds up to level floor((log2 N - 1)/2) and fails
+    above (N = 4096: 129^2 = 257 mod 8192); an expansion over 8 levels with
+    keys only for levels 5..7 decrypts to the same indicators."""
+    prm = tiny_params
+    b = O.pir_key_base(prm, 8)
+    assert b == 5 and O.pir_galois(prm, 5) == 129 and pow(129, 2, 2 * prm.N) == 257
+    for a in range(1, b + 1):
+        assert pow(O.pir_galois(prm, a), 2, 2 * prm.N) == O.pir_galois(prm, a - 1)
+    assert pow(O.pir_galois(prm, b + 1), 2, 2 * prm.N) != O.pir_galois(prm, b)
+    levels, row = 8, 77
+    cr = W.pir_client_randomness(1, levels, prm.N, prm.q, prm.P, seed=45)
+    keys = [O.keygen(prm, cr.secret[0], O.pir_galois(prm, a), cr.key_a[0, a], cr.key_e[0, a]) for a in range(b, levels)]
+    ct = O.encrypt(prm, cr.secret[0], O.pir_query_plaintext(prm, row, levels), cr.enc_a[0], cr.enc_e[0])
+    ind = O.pir_expand(prm, ct, keys, levels, derive=True)
+    for k in (0, row, 255):
+        m, _ = O.decrypt_poly(prm, cr.secret[0], ind[k])
+        want = np.zeros(prm.N, np.int64)
+        want[0] = 1 if k == row else 0
+        assert np.array_equal(np.asarray(m, np.int64), want), k

@@ -302,6 +302,20 @@ int wally_pir_answer2(wally_ctx *ctx, uint32_t n, const uint64_t *queries, const
 int wally_keygen_relin(wally_ctx *ctx, uint32_t n, const int8_t *secret, const uint64_t *key_a, const int8_t *key_e,
                        uint64_t *keys, void *stream);
 
+/* Sec. 4.2 "Reducing evaluation key size": (N/2^a + 1)^2 = N/2^(a-1) + 1
+ * (mod 2N) while a <= floor((log2 N - 1) / 2), so with derivation enabled the
+ * client sends only the keys of levels b .. c-1, b = min(c - 1,
+ * floor((log2 N - 1) / 2)), and the server reaches every level a < b by
+ * substituting 2^(b - a) times with the key of level b.  The keys arguments
+ * of wally_pir_answer / wally_pir_answer2 then hold c - b keys a query
+ * (levels b .. c-1).  Off by default; it changes the answer's bits (more
+ * key switches), not what it decrypts to. */
+int wally_pir_derive_keys(wally_ctx *ctx, int enable);
+
+/* The expansion levels whose keys the client sends for the loaded table:
+ * *first .. *first + *count - 1 (two_dims: for wally_pir_answer2). */
+int wally_pir_key_levels(const wally_ctx *ctx, int two_dims, uint32_t *first, uint32_t *count);
+
 /* Client side of the PIR.  Galois keys for a list of elements (at most 16):
  * galois (host) [num_keys], odd, < 2N; key_a device [n][num_keys][L][L+1][N],
  * key_e device int8 [n][num_keys][L][N]; keys device [n][num_keys][L][2][L+1][N]

@@ -242,6 +242,7 @@ struct wally_ctx {
     // index PIR: the table (NTT form, times 2^64), the monomials X^(-2^a),
     // and the expansion scratch
     uint32_t pir_rows = 0, pir_cols = 0, pir_levels = 0, pir_levels2 = 0;
+    bool pir_derive = false;  // lower expansion keys derived by repeated substitution
     DevBuf<u64> pir_db, pir_mono, pir_E[2], pir_S, pir_keys, pir_out, pir_sc, pir_dg, pir_u, pir_dd;
     DevBuf<u32> pir_map;
     // MulPIR's second dimension: the extension basis (its own context for
@@ -716,9 +717,19 @@ void release_waves(wally_ctx *c)
 // Oblivious expansion of nq queries over lv levels: pir_E[0] holds their
 // NTT-form ciphertexts and pir_keys their keys (NTT form); on return
 // pir_E[cur] holds [nq][2^lv] indicator ciphertexts.
+// First expansion level whose key the client sends: 0, or with derived keys
+// b = min(lv - 1, floor((log2 N - 1) / 2)), below which (N/2^a + 1)^2 =
+// N/2^(a-1) + 1 (mod 2N) lets the key of level b serve every lower level.
+uint32_t pir_key_base(const wally_ctx *c, uint32_t lv)
+{
+    if (!c->pir_derive || lv == 0) return 0;
+    return std::min(lv - 1, (c->log_n - 1) / 2);
+}
+
 int pir_expand(wally_ctx *c, uint32_t nq, uint32_t lv, int &cur, cudaStream_t st)
 {
     const size_t N = c->N, L = c->L, ctw = c->ctw(), keyw = c->keysw() / 2;
+    const uint32_t b = pir_key_base(c, lv), nkeys = lv - b;
     cur = 0;
     for (uint32_t a = 0; a < lv; a++) {
         const u32 count = nq << a;
@@ -729,16 +740,21 @@ int pir_expand(wally_ctx *c, uint32_t nq, uint32_t lv, int &cur, cudaStream_t st
         r.src_stride = ctw;
         r.dst = c->pir_S.p;
         r.dst_stride = ctw;
-        r.key = c->pir_keys.p + (size_t)a * keyw;
-        r.key_stride = (size_t)lv * keyw;
+        r.key = c->pir_keys.p + (size_t)(a < b ? 0 : a - b) * keyw;
+        r.key_stride = (size_t)nkeys * keyw;
         r.key_map = c->pir_map.p;
         r.n_max = count;
-        r.galois = (uint64_t)(N >> a) + 1;
+        r.galois = (uint64_t)(N >> (a < b ? b : a)) + 1;
         r.sc = c->pir_sc.p;
         r.dg = c->pir_dg.p;
         r.u = c->pir_u.p;
         r.dd = c->pir_dd.p;
         CUDA_TRY(launch_rotate(c->dp, r, st, c->pr()));
+        // a level below b: the substitution of level b applied 2^(b - a) times
+        for (uint32_t rep = 1; a < b && rep < (1u << (b - a)); rep++) {
+            r.src = c->pir_S.p;
+            CUDA_TRY(launch_rotate(c->dp, r, st, c->pr()));
+        }
         CUDA_TRY(launch_pir_combine(c->dp, c->pir_E[cur].p, c->pir_S.p, c->pir_E[cur ^ 1].p,
                                     c->pir_mono.p + (size_t)a * L * N, count, a, st));
         cur ^= 1;
@@ -1547,9 +1563,10 @@ int wally_pir_answer(wally_ctx *c, uint32_t n, const uint64_t *queries, const ui
         // queries and keys to NTT form (keys times 2^64)
         CUDA_TRY(launch_to_ntt(c->dp, nullptr, queries + (size_t)q0 * ctw, ctw, c->pir_E[0].p, ctw, 2 * (u32)L,
                                (u32)L, nq, nullptr, false, st));
+        const uint32_t nkeys = lv - pir_key_base(c, lv);
         if (lv)
-            CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)q0 * lv * keyw, keyw, c->pir_keys.p, keyw,
-                                   2 * (u32)(L * (L + 1)), (u32)(L + 1), nq * lv, nullptr, true, st));
+            CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)q0 * nkeys * keyw, keyw, c->pir_keys.p, keyw,
+                                   2 * (u32)(L * (L + 1)), (u32)(L + 1), nq * nkeys, nullptr, true, st));
         int cur = 0;
         int rc = pir_expand(c, nq, lv, cur, st);
         if (rc) return rc;
@@ -1708,8 +1725,9 @@ int wally_pir_answer2(wally_ctx *c, uint32_t n, const uint64_t *queries, const u
         const uint32_t nq = std::min(chunk, n - q0);
         CUDA_TRY(launch_to_ntt(c->dp, nullptr, queries + (size_t)q0 * ctw, ctw, c->pir_E[0].p, ctw, 2 * (u32)L,
                                (u32)L, nq, nullptr, false, st));
-        CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)q0 * lv * keyw, keyw, c->pir_keys.p, keyw,
-                               2 * (u32)(L * (L + 1)), (u32)(L + 1), nq * lv, nullptr, true, st));
+        const uint32_t nkeys = lv - pir_key_base(c, lv);
+        CUDA_TRY(launch_to_ntt(c->dp, nullptr, keys + (size_t)q0 * nkeys * keyw, keyw, c->pir_keys.p, keyw,
+                               2 * (u32)(L * (L + 1)), (u32)(L + 1), nq * nkeys, nullptr, true, st));
         int cur = 0;
         rc = pir_expand(c, nq, lv, cur, st);
         if (rc) return rc;
@@ -1758,6 +1776,24 @@ int wally_pir_answer2(wally_ctx *c, uint32_t n, const uint64_t *queries, const u
         CUDA_TRY(launch_rotate(c->dp, r, st, c->pr()));
         CUDA_TRY(launch_from_ntt(c->dp, c->pd_out.p, out + (size_t)q0 * ctw, 2 * (u32)L, (u32)L, nq, st));
     }
+    return WALLY_OK;
+}
+
+int wally_pir_derive_keys(wally_ctx *c, int enable)
+{
+    if (!c) return fail(WALLY_EINVAL, "null context");
+    c->pir_derive = enable != 0;
+    return WALLY_OK;
+}
+
+int wally_pir_key_levels(const wally_ctx *c, int two_dims, uint32_t *first, uint32_t *count)
+{
+    if (!c || !first || !count) return fail(WALLY_EINVAL, "null argument");
+    if (!c->pir_rows) return fail(WALLY_ESTATE, "no PIR table loaded");
+    const uint32_t lv = two_dims ? c->pir_levels2 : c->pir_levels;
+    if (two_dims && !lv) return fail(WALLY_EINVAL, "rows + columns must be at most 4096");
+    *first = pir_key_base(c, lv);
+    *count = lv - *first;
     return WALLY_OK;
 }
 

@@ -95,6 +95,8 @@ SIGNATURES = {
     "wally_pir_answer": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp]),
     "wally_keygen_galois": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "wally_pir_answer2": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
+    "wally_pir_derive_keys": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "wally_pir_key_levels": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     "wally_keygen_relin": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "wally_encrypt_poly": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "wally_decrypt_poly": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
@@ -310,6 +312,17 @@ def wally_pir_answer2(ctx: int, n: int, queries, keys, relin_keys, out, stream=N
     _require_cuda(queries, keys, relin_keys, out)
     _check(load().wally_pir_answer2(ctx, n, _ptr(queries), _ptr(keys), _ptr(relin_keys), _ptr(out),
                                     _stream(stream)))
+
+
+def wally_pir_derive_keys(ctx: int, enable: bool) -> None:
+    _check(load().wally_pir_derive_keys(ctx, 1 if enable else 0))
+
+
+def wally_pir_key_levels(ctx: int, two_dims: bool = False) -> tuple[int, int]:
+    """(first level, number of levels) whose keys the client sends."""
+    f, c = _u32(), _u32()
+    _check(load().wally_pir_key_levels(ctx, 1 if two_dims else 0, ctypes.byref(f), ctypes.byref(c)))
+    return f.value, c.value
 
 
 def wally_keygen_relin(ctx: int, n: int, secret, key_a, key_e, keys, stream=None) -> None:

@@ -178,3 +178,43 @@ def test_pir_two_dimensions(rows, cols, nq):
     ref = O.pir_second_dimension(prm, first, ind[rows:rows + cols], Wl.to_u64_numpy(rlk[0]))
     assert np.array_equal(Wl.to_u64_numpy(out[0]), ref)
     ctx.close()
+
+
+def test_pir_answer_with_derived_keys():
+    """Key derivation (Sec. 4.2): at N = 4096 a 200-row table needs 8 levels;
+    the client sends the keys of levels 5..7 only, the server substitutes
+    2^(5-a) times with the level-5 key below; bit for bit against the
+    oracle's derived expansion, and decrypted."""
+    prm, ctx = _setup("tiny")
+    rows, cols, levels = 200, 2, 8
+    db = W.pir_plaintexts(rows, cols, prm.N, prm.t, seed=57)
+    Wl.wally_pir_load(ctx.ptr, db)
+    Wl.wally_pir_derive_keys(ctx.ptr, True)
+    first, count = Wl.wally_pir_key_levels(ctx.ptr)
+    assert (first, count) == (5, 3) and first == O.pir_key_base(prm, levels)
+    wanted = [137, 4]
+    n = len(wanted)
+    cr = W.pir_client_randomness(n, levels, prm.N, prm.q, prm.P, seed=58)
+    sec = torch.from_numpy(cr.secret).to(DEV)
+    keys = torch.empty((n, count, prm.L, 2, prm.L + 1, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_keygen_galois(ctx.ptr, n, [O.pir_galois(prm, a) for a in range(first, levels)], sec,
+                           Wl.u64_tensor(np.ascontiguousarray(cr.key_a[:, first:]), DEV),
+                           torch.from_numpy(np.ascontiguousarray(cr.key_e[:, first:])).to(DEV), keys)
+    m = np.stack([O.pir_query_plaintext(prm, r, levels) for r in wanted])
+    cts = torch.empty((n, 2, prm.L, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_encrypt_poly(ctx.ptr, n, sec, Wl.u64_tensor(m, DEV), Wl.u64_tensor(cr.enc_a, DEV),
+                          torch.from_numpy(cr.enc_e).to(DEV), cts)
+    out = torch.empty((n, cols, 2, prm.L, prm.N), dtype=torch.int64, device=DEV)
+    Wl.wally_pir_answer(ctx.ptr, n, cts, keys, out)
+    Wl.wally_sync(ctx.ptr)
+    got = Wl.to_u64_numpy(out)
+    kg = Wl.to_u64_numpy(keys[0])
+    ind = O.pir_expand(prm, Wl.to_u64_numpy(cts[0]), [kg[a] for a in range(count)], levels, derive=True)
+    assert np.array_equal(got[0], O.pir_first_dimension(prm, db, ind))
+    coeffs = torch.empty((n * cols, prm.N), dtype=torch.int64, device=DEV)
+    idx = torch.tensor([i for i in range(n) for _ in range(cols)], dtype=torch.int32, device=DEV)
+    Wl.wally_decrypt_poly(ctx.ptr, n * cols, sec, idx, out.reshape(n * cols, 2, prm.L, prm.N), coeffs)
+    dec = coeffs.cpu().numpy().reshape(n, cols, prm.N)
+    for i, r in enumerate(wanted):
+        assert np.array_equal(dec[i], db[r].astype(np.int64)), i
+    ctx.close()

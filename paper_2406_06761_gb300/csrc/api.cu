@@ -58,6 +58,10 @@ template <typename T>
 struct DevBuf {
     T *p = nullptr;
     size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
     cudaError_t ensure(size_t count)
     {
         if (count <= n) return cudaSuccess;
@@ -85,6 +89,10 @@ template <typename T>
 struct PinnedBuf {
     T *p = nullptr;
     size_t n = 0;
+    PinnedBuf() = default;
+    PinnedBuf(const PinnedBuf &) = delete;
+    PinnedBuf &operator=(const PinnedBuf &) = delete;
+    ~PinnedBuf() { release(); }
     cudaError_t ensure(size_t count)
     {
         if (count <= n) return cudaSuccess;

@@ -718,3 +718,28 @@ def test_pir_key_derivation_by_squaring(tiny_params):
         want = np.zeros(prm.N, np.int64)
         want[0] = 1 if k == row else 0
         assert np.array_equal(np.asarray(m, np.int64), want), k
+
+
+def test_noise_of_additions_and_plaintext_products(tiny_params):
+    """Noise invariants of Sec. 2 (Table of operations: addition adds the
+    noises, PtCtMult multiplies them by about N ||P||): with e the noise of
+    c0 + c1 s - Delta m,
+      ||e(a + b)|| <= ||e(a)|| + ||e(b)|| + t           (the carry of m_a + m_b past t costs [Q]_t < t)
+      ||e(P a)||   <= N ||P||_inf ||e(a)|| + N t^2 / 4  (centred P; the carry of P m_a past t)."""
+    prm = tiny_params
+    cr = W.client_randomness(2, prm.N, prm.q, prm.P, seed=66)
+    rng = np.random.default_rng(66)
+    ma, mb, pv = (rng.integers(0, prm.t, prm.N, dtype=np.uint64) for _ in range(3))
+    a = O.encrypt(prm, cr.secret[0], ma, cr.enc_a[0], cr.enc_e[0])
+    b = O.encrypt(prm, cr.secret[0], mb, cr.enc_a[1], cr.enc_e[1])
+    ea, eb = (2.0 ** O.noise_bits(prm, cr.secret[0], c) for c in (a, b))
+    s = O._ct_add(prm, a, b, +1)
+    m, _ = O.decrypt_poly(prm, cr.secret[0], s)
+    assert np.array_equal(np.asarray(m, np.uint64), (ma + mb) % np.uint64(prm.t))
+    assert 2.0 ** O.noise_bits(prm, cr.secret[0], s) <= ea + eb + prm.t
+    P = O.lift_plaintext(prm, pv)
+    pa = O.ptct_sum(prm, P[None], a[None])
+    m, _ = O.decrypt_poly(prm, cr.secret[0], pa)
+    assert np.array_equal(np.asarray(m, np.uint64), O.polymul(prm, prm.L + 1, pv, ma))
+    pinf = prm.t // 2
+    assert 2.0 ** O.noise_bits(prm, cr.secret[0], pa) <= prm.N * pinf * ea + prm.N * prm.t ** 2 / 4

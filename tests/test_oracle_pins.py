@@ -743,3 +743,41 @@ def test_noise_of_additions_and_plaintext_products(tiny_params):
     assert np.array_equal(np.asarray(m, np.uint64), O.polymul(prm, prm.L + 1, pv, ma))
     pinf = prm.t // 2
     assert 2.0 ** O.noise_bits(prm, cr.secret[0], pa) <= prm.N * pinf * ea + prm.N * prm.t ** 2 / 4
+
+
+@pytest.mark.parametrize("log_n", [3, 6])
+def test_polymul_matches_convolution_other_sizes(log_n):
+    """NTT products against the folded linear convolution at N = 8 and 64."""
+    prm = O.params(log_n, 2, 30, 10, 4)
+    for j in range(prm.L + 1):
+        p = prm.mods[j]
+        a, b = _rand_poly(p, prm.N, 30 + j), _rand_poly(p, prm.N, 40 + j)
+        full = np.convolve(a.astype(object), b.astype(object))
+        ref = [(int(full[k]) - (int(full[k + prm.N]) if k + prm.N < len(full) else 0)) % p for k in range(prm.N)]
+        assert [int(v) for v in O.polymul(prm, j, a, b)] == ref
+
+
+@pytest.mark.parametrize("name", ["tiny", "batched", "serving", "full_scale", "wide"])
+def test_scores_cannot_wrap_around_t(name):
+    """Sec. 7's no-wrap condition for the workloads: the largest possible
+    dot product d * bound^2 stays below (t - 1)/2, so decrypted scores are
+    the exact integers, not residues."""
+    w = W.WORKLOADS[name]
+    prm = O.params(w.log_n, w.num_q, w.q_bits, w.t_bits, w.dim)
+    assert w.dim * w.entry_bound ** 2 < (prm.t - 1) // 2
+
+
+def test_fake_query_counts_follow_the_negative_binomial():
+    """Alg. "Client Query Generation": NB(r = 0.5, p = 0.9) fake queries per
+    client: sample mean and variance against r(1-p)/p and r(1-p)/p^2, and
+    infinite divisibility (Sec. 8): the sum over U clients of NB(r/U, p) has
+    the mean and variance of one NB(r, p)."""
+    r, p, n = 0.5, 0.9, 400_000
+    c = W.fake_counts(n, r, p, seed=3)
+    mean, var = r * (1 - p) / p, r * (1 - p) / p ** 2
+    assert abs(c.mean() - mean) < 5 * np.sqrt(var / n)
+    assert abs(c.var() - var) / var < 0.05
+    U = 8
+    parts = sum(W.fake_counts(n, r / U, p, seed=10 + u) for u in range(U))
+    assert abs(parts.mean() - mean) < 5 * np.sqrt(var / n)
+    assert abs(parts.var() - var) / var < 0.05

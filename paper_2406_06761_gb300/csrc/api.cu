@@ -15,6 +15,7 @@
 #include "kernels.hpp"
 #include "ctx_access.hpp"
 #include "pir.hpp"
+#include "plan.hpp"
 
 using namespace wally;
 
@@ -507,56 +508,6 @@ int run_wave(wally_ctx *c, Lane &ln, const WavePlan &wp, uint32_t wave_len, cons
 }
 
 // ---------------------------------------------------------------- compact cluster store
-// One wave of a call: positions [begin, begin + len) of the cluster-sorted
-// order and, with the compact store, the nz chunks (list entries z_off ..)
-// that its queries name.
-struct Wave {
-    uint32_t begin, len, z_off, nz;
-};
-
-// Fixed waves of at most W positions (the NTT store).
-void fixed_waves(uint32_t n, uint32_t W, std::vector<Wave> &waves)
-{
-    waves.clear();
-    for (uint32_t wb = 0; wb < n; wb += W) waves.push_back(Wave{wb, std::min(W, n - wb), 0, 0});
-}
-
-// Compact store: cluster k holds positions [start_k, start_k + cnt[k]) of the
-// sorted order (clusters in id order).  A wave ends at W queries or where
-// its clusters would need more than cache_chunks encoded chunks; a cluster
-// split between waves is encoded in each.  zc / zk: (cluster, chunk) of every
-// wave's chunks, a cluster's chunks consecutive.
-void compact_waves(const wally_ctx *c, const uint32_t *cnt, uint32_t W, std::vector<Wave> &waves,
-                   std::vector<uint32_t> &zc, std::vector<uint32_t> &zk)
-{
-    waves.clear();
-    zc.clear();
-    zk.clear();
-    const uint32_t C = c->cache_chunks;
-    uint32_t pos = 0;
-    Wave cur{0, 0, 0, 0};
-    for (uint32_t k = 0; k < c->num_clusters; k++) {
-        uint32_t rem = cnt[k];
-        const uint32_t m = c->h_chunks[k];
-        while (rem) {
-            if (cur.len == W || cur.nz + m > C) {
-                waves.push_back(cur);
-                cur = Wave{pos, 0, (uint32_t)zc.size(), 0};
-            }
-            const uint32_t take = std::min(rem, W - cur.len);
-            for (uint32_t j = 0; j < m; j++) {
-                zc.push_back(k);
-                zk.push_back(j);
-            }
-            cur.nz += m;
-            cur.len += take;
-            rem -= take;
-            pos += take;
-        }
-    }
-    if (cur.len) waves.push_back(cur);
-}
-
 // Copy the chunk lists to the device (ln.zlist: [2][total], clusters then
 // chunk indices) through the lane's pinned buffer, on `st`.
 int upload_chunk_list(Lane &ln, const std::vector<uint32_t> &zc, const std::vector<uint32_t> &zk, cudaStream_t st)
@@ -641,7 +592,7 @@ int eval_device(wally_ctx *c, Lane *const *lanes, const cudaStream_t *streams, i
         if (l0.h_counts.ensure(K) != cudaSuccess) return fail(WALLY_ENOMEM, "cannot allocate the host counts");
         CUDA_TRY(cudaMemcpyAsync(l0.h_counts.p, l0.counts.p, 4 * (size_t)K, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        compact_waves(c, l0.h_counts.p, W, waves, zc, zk);
+        compact_waves(c->h_chunks.data(), c->num_clusters, c->cache_chunks, l0.h_counts.p, W, waves, zc, zk);
         int rc = upload_chunk_list(l0, zc, zk, st);
         if (rc) return rc;
     } else {
@@ -1253,7 +1204,7 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
     if (c->compact()) {
         std::vector<uint32_t> cnt(K);
         for (uint32_t k = 0; k < K; k++) cnt[k] = start[k + 1] - start[k];
-        compact_waves(c, cnt.data(), W, waves, zc, zk);
+        compact_waves(c->h_chunks.data(), c->num_clusters, c->cache_chunks, cnt.data(), W, waves, zc, zk);
         rc = upload_chunk_list(ln, zc, zk, st);
         if (rc) return rc;
     } else {

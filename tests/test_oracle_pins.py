@@ -268,6 +268,55 @@ def test_cluster_encoding_two_chunks_and_padding():
     assert dec[0, 0, 1][99] == 0
 
 
+def _expected_slots(prm, E, k, i, b):
+    """Slot values of P'_{k,i,b} written out from the layout of Sec. 4.1
+    (chunk k, slot s = beta*d_pad + x holds embedding k*N + s, diagonal j
+    takes column (x + j) mod d_pad) and the BSGS pre-rotation of Alg.
+    "Server Initialization" (row rotation right by g*i), as integers."""
+    N, half, dp = prm.N, prm.N // 2, prm.d_pad
+    j = prm.g * i + b
+    p = np.zeros(N, dtype=np.int64)
+    for s in range(N):
+        u, col = k * N + s, (s % dp + j) % dp
+        if u < len(E) and col < prm.d:
+            p[s] = int(E[u][col])
+    out = np.empty(N, dtype=np.int64)
+    sh = (prm.g * i) % half
+    for s in range(N):
+        rho, c = divmod(s, half)
+        out[s] = p[rho * half + (c - sh) % half]
+    return out
+
+
+@pytest.mark.parametrize("which", ["small", "tiny"])
+def test_cluster_encoding_lift_is_centred(which, small_params, tiny_params):
+    """Reading R9 (the plaintext lift, on which the paper is silent): each
+    encoded plaintext, CRT-composed over its L limbs and read as an integer
+    in (-Q/2, Q/2], lies in [-(t-1)/2, (t-1)/2] (the centred representative,
+    not [0, t)), and decodes mod t to the pre-rotated diagonal it encodes.
+    A lift into [0, t) or a dropped limb reduction fails the first check; a
+    wrong diagonal, packing or pre-rotation fails the second."""
+    prm = small_params if which == "small" else tiny_params
+    t, Q = prm.t, 1
+    for q in prm.q:
+        Q *= int(q)
+    E = W.embeddings(11 if which == "small" else 700, prm.d, 15, seed=9)
+    m, pt = O.encode_cluster(prm, E)
+    picks = [(k, i, b) for k in range(m) for i in range(prm.h) for b in range(prm.g)]
+    if which == "tiny":
+        picks = [(0, 0, 0), (0, 0, 5), (0, 3, 1), (0, prm.h - 1, prm.g - 1)]
+    seen_negative = False
+    for k, i, b in picks:
+        x = B.poly_crt([pt[k, i, b, l] for l in range(prm.L)], [int(q) for q in prm.q])
+        x = [v - Q if v > Q // 2 else v for v in x]
+        assert all(-(t - 1) // 2 <= v <= (t - 1) // 2 for v in x), (k, i, b)
+        seen_negative |= any(v < 0 for v in x)
+        dec = O.slots_decode(prm, np.array([v % t for v in x], dtype=np.uint64)).astype(np.int64)
+        dec = np.where(dec > t // 2, dec - t, dec)
+        assert np.array_equal(dec, _expected_slots(prm, E, k, i, b)), (k, i, b)
+    assert seen_negative  # the centred range is used, not only its upper half
+
+
 # ------------------------------------------------------------------ client
 
 def test_encrypt_decrypt_roundtrip(tiny_params):

@@ -45,7 +45,7 @@ enum {
     WALLY_EINVAL = 1,   /* bad argument: shape, range, null pointer, unsupported size */
     WALLY_ENOMEM = 2,   /* device or host allocation failed */
     WALLY_ECUDA = 3,    /* a CUDA runtime call failed */
-    WALLY_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    WALLY_ETIMEOUT = 4, /* a bounded device-side wait gave up (reserved: no call waits on the device) */
     WALLY_ESTATE = 5    /* call out of order (e.g. eval before load_clusters) */
 };
 
@@ -209,9 +209,13 @@ int wally_rotate(wally_ctx *ctx, uint32_t n, uint64_t galois_elt, const uint64_t
  * Its scratch is one static device array of WALLY_NOALLOC_SCRATCH_BYTES that
  * every GPU loading the library keeps until exit; n is limited to
  *   WALLY_NOALLOC_SCRATCH_BYTES / (8 N (7L + 2 + 3L(L+1)))
- * ciphertexts (4 at N = 8192, L = 3); larger n returns WALLY_EINVAL.  The
- * first call on a device looks up the array's device address (set-up), so
- * make it before any stream capture.  All calls share the array: calls whose
+ * ciphertexts (4 at N = 8192, L = 3); larger n returns WALLY_EINVAL.  At
+ * N = 16384, L = 6 one ciphertext needs 22.3 MB, more than the array holds,
+ * so every call with those parameters returns WALLY_EINVAL.  The first call
+ * on a device looks up the array's device address (set-up) and keeps it for
+ * the life of the process, so make it before any stream capture, and do not
+ * reset the device (cudaDeviceReset) while the library is loaded: the kept
+ * address would then be stale.  All calls share the array: calls whose
  * work overlaps on the GPU (other streams, other contexts on the device) race
  * and must be serialised by the caller.  Asynchronous on `stream`. */
 #define WALLY_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -339,7 +343,10 @@ int wally_decrypt_poly(wally_ctx *ctx, uint32_t n, const int8_t *secret, const u
  * paper has no counterpart).  wally_profile_enable(ctx, 1) starts a fresh
  * collection, 0 stops it.  wally_profile_read synchronises the device, sums
  * launches and milliseconds per kernel kind into out[0 .. *count) (at most
- * cap entries) and clears the collection. */
+ * cap entries) and clears the collection.  Launches captured in a CUDA graph
+ * while profiling is on record their events as external nodes of the graph:
+ * every replay rewrites them, and a read after replays reports the latest
+ * replay (the same holds for wally_profile_waves). */
 typedef struct {
     char name[16];       /* to_ntt, ks_a, ks_b, ks_c, mac, output, plan, encode (compact store) */
     uint64_t launches;
@@ -349,13 +356,46 @@ typedef struct {
 int wally_profile_enable(wally_ctx *ctx, int enable);
 int wally_profile_read(wally_ctx *ctx, wally_kernel_time *out, uint32_t cap, uint32_t *count);
 
+/* Completion time of every wave of the evaluation calls (wally_eval_batch,
+ * wally_eval_batch_lane, wally_eval_batch_host) made while profiling is on
+ * (measurement only; the paper has no counterpart): for wave w in submission
+ * order, call[w] = index of its call (0 = the first call since profiling was
+ * enabled), queries[w] = the queries it evaluated, done_ms[w] = milliseconds
+ * from the start of that call (an event recorded on the call's stream at its
+ * entry) to the wave's outputs being written.  A query's latency inside a
+ * batch is its wave's done_ms.  Synchronises the device, writes at most cap
+ * entries of each non-NULL array, sets *count to the number of waves, and
+ * clears the wave records (wally_profile_read does not clear them). */
+int wally_profile_waves(wally_ctx *ctx, uint32_t cap, uint32_t *call, uint32_t *queries, float *done_ms,
+                        uint32_t *count);
+
 /* Throughput ceiling of the integer primitives on `device` (all SMs busy,
  * independent operations, no memory traffic): 64-bit Shoup modular
- * multiplications, NTT butterflies (one Shoup product plus three
- * additions/comparisons), and 64x64 -> 128-bit multiply-accumulates, each in
+ * multiplications, NTT butterflies (the forward butterfly the transforms
+ * use: one Shoup product written out in 32-bit multiply-adds plus three
+ * 64-bit additions), and 64x64 -> 128-bit multiply-accumulates, each in
  * operations per second.  Used as the denominator of the integer-ALU
  * roofline.  Synchronous; allocates a few kilobytes. */
 int wally_measure_int_peaks(int32_t device, double *modmul_per_s, double *butterfly_per_s, double *mac128_per_s);
+
+/* Issue rates of the 32-bit instructions the modular arithmetic is built from
+ * (observability; the paper has no counterpart), each with all SMs busy and
+ * enough independent operations to keep the pipe full, in operations per
+ * second: mad.lo.u32, mul.hi.u32 and mad.wide.u32 (all on the integer
+ * multiplier).  sm_clock_hz: the SM clock (clock64 ticks of a CTA over the
+ * event time of a launch of one CTA an SM).  bfly_ceiling_per_s: the rate at which the
+ * multiplier could retire NTT butterflies if it did nothing else -- one
+ * butterfly issues two mul.hi, three mad.wide and four mad.lo, so the
+ * ceiling is 1 / (2/mul_hi + 3/mad_wide + 4/mad_lo).  Synchronous. */
+typedef struct {
+    double mad_lo_per_s;
+    double mul_hi_per_s;
+    double mad_wide_per_s;
+    double sm_clock_hz;
+    double bfly_ceiling_per_s;
+} wally_pipe_rates;
+
+int wally_measure_pipe_rates(int32_t device, wally_pipe_rates *out);
 
 /* ---------------------------------------------------------------- launch shapes
  * The paper has no counterpart: these choose how the batch is laid onto this
@@ -371,18 +411,24 @@ int wally_measure_int_peaks(int32_t device, double *modmul_per_s, double *butter
  *   ntt_ctas_per_sm  0: as many transform-kernel CTAs per SM as shared memory
  *                    allows; k > 0: at most k (they are launched with more
  *                    shared memory than they use)
- * Defaults: 1024 (or the max_wave of wally_params), 2, 3, 0. */
+ *   ks_core          the NTT shape of the key-switch kernels: 0 = passes of
+ *                    1 + 4 + 4 + 4 stages (N = 8192) over a shared-memory
+ *                    polynomial, 16 coefficients a thread at a time, three
+ *                    CTAs an SM; 1 = passes of 5 + 5 + 3 stages on 32
+ *                    coefficients held in registers, two CTAs an SM
+ * Defaults: 1024 (or the max_wave of wally_params), 2, 3, 0, 0. */
 typedef struct {
     uint32_t max_wave;
     uint32_t lanes;
     uint32_t mac_ctas_per_sm;
     uint32_t ntt_ctas_per_sm;
+    uint32_t ks_core;
 } wally_tuning;
 
 int wally_get_tuning(const wally_ctx *ctx, wally_tuning *out);
 
 /* Errors: WALLY_EINVAL (max_wave 0, lanes not 1 or 2, mac_ctas_per_sm not
- * 1..3).  An ntt_ctas_per_sm at or above what shared memory allows anyway is
+ * 1..3, ks_core not 0 or 1).  An ntt_ctas_per_sm at or above what shared memory allows anyway is
  * no cap.  Takes effect at the next call; it must not overlap running
  * evaluations of the context. */
 int wally_set_tuning(wally_ctx *ctx, const wally_tuning *tuning);
@@ -393,8 +439,9 @@ int wally_set_tuning(wally_ctx *ctx, const wally_tuning *tuning);
  * in the context and returns its index in *best.  With candidates non-NULL
  * the candidates are candidates[0 .. num_candidates).  With candidates NULL
  * (num_candidates 0) the search is staged: max_wave in {512, 1024, 2048} x
- * lanes in {1, 2} with mac 3, ntt 0; then, at the best of those,
- * mac_ctas_per_sm in {2, 3} x ntt_ctas_per_sm in {0, 2} (9 shapes in all).
+ * lanes in {1, 2} with mac 3, ntt 0, ks_core 0; then, at the best of those,
+ * mac_ctas_per_sm in {2, 3} x ntt_ctas_per_sm in {0, 2}; then the best of
+ * all with ks_core 1 (10 shapes in all).
  * tried (host, [WALLY_AUTOTUNE_MAX] or [num_candidates], may be NULL)
  * receives the shapes in the order timed, ms_per_query (same length, may be
  * NULL) their mean device milliseconds per query of the sample, or -1 where

@@ -116,7 +116,20 @@ struct PinnedBuf {
     }
 };
 
-// Per-launch CUDA events, summed per kernel kind when read.
+// Record e on st; inside a stream capture as an external event node, so that
+// every replay of the graph writes the event's timestamp (read after the
+// replay like any recorded event).
+void record_event(cudaEvent_t e, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
+
+// Per-launch CUDA events, summed per kernel kind when read.  Launches
+// captured in a CUDA graph are timed by the graph's latest replay.
 struct EventProfiler : Profiler {
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
@@ -138,12 +151,12 @@ struct EventProfiler : Profiler {
     void begin(int kind, cudaStream_t st) override
     {
         open_[kind] = take();
-        cudaEventRecord(open_[kind], st);
+        record_event(open_[kind], st);
     }
     void end(int kind, cudaStream_t st) override
     {
         cudaEvent_t e = take();
-        cudaEventRecord(e, st);
+        record_event(e, st);
         recs.push_back({kind, open_[kind], e});
     }
     void reset()
@@ -151,9 +164,48 @@ struct EventProfiler : Profiler {
         used = 0;
         recs.clear();
     }
+    // completion of every wave of the evaluation calls (their own event pool:
+    // reading the kernel times does not recycle them)
+    struct WaveRec {
+        uint32_t call, queries;
+        cudaEvent_t done;
+    };
+    std::vector<cudaEvent_t> wpool;
+    size_t wused = 0;
+    std::vector<cudaEvent_t> call_start;
+    std::vector<WaveRec> waves;
+    cudaEvent_t wtake()
+    {
+        if (wused == wpool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            wpool.push_back(e);
+        }
+        return wpool[wused++];
+    }
+    void call_begin(cudaStream_t st)
+    {
+        cudaEvent_t e = wtake();
+        record_event(e, st);
+        call_start.push_back(e);
+    }
+    void wave_end(cudaStream_t st, uint32_t queries)
+    {
+        if (call_start.empty()) return;
+        cudaEvent_t e = wtake();
+        record_event(e, st);
+        waves.push_back({(uint32_t)call_start.size() - 1, queries, e});
+    }
+    void reset_waves()
+    {
+        wused = 0;
+        call_start.clear();
+        waves.clear();
+    }
     ~EventProfiler()
     {
         for (cudaEvent_t e : pool) cudaEventDestroy(e);
+        for (cudaEvent_t e : wpool) cudaEventDestroy(e);
     }
 };
 
@@ -584,6 +636,7 @@ int eval_device(wally_ctx *c, Lane *const *lanes, const cudaStream_t *streams, i
     if (l0.counts.ensure(K) != cudaSuccess || l0.cstart.ensure(K + 1) != cudaSuccess ||
         l0.fill.ensure(K) != cudaSuccess || l0.sorted_q.ensure(n) != cudaSuccess)
         return fail(WALLY_ENOMEM, "cannot allocate the grouping arrays");
+    if (c->prof_on) c->prof.call_begin(st);
     // a0: group by cluster (shared by the lanes)
     CUDA_TRY(launch_group(ids, n, K, l0.counts.p, l0.cstart.p, l0.fill.p, l0.sorted_q.p, c->d_err, st));
     std::vector<Wave> waves;
@@ -613,6 +666,7 @@ int eval_device(wally_ctx *c, Lane *const *lanes, const cudaStream_t *streams, i
         if (c->compact()) rc = encode_wave(c, ln, wv, l0.zlist.p, zc.size(), s);
         if (rc == WALLY_OK) rc = run_wave(c, ln, ln.wp, wv.len, wave_store(c, ln), s);
         if (rc) return rc;
+        if (c->prof_on) c->prof.wave_end(s, wv.len);
     }
     if (nl > 1) {
         CUDA_TRY(cudaEventRecord(c->join_ev, streams[1]));
@@ -631,7 +685,7 @@ uint32_t ntt_smem_for(const wally_ctx *c, uint32_t k)
     const int per = c->smem_per_sm / (int)(k + 1) - c->smem_reserved;  // k + 1 CTAs must not fit
     uint32_t dyn = per > 0 ? ((uint32_t)per + 15u) & ~15u : 0;
     if (dyn <= need) return 0;  // the need alone already limits the CTAs
-    if (dyn > 226u * 1024u) return 0;  // the most the transform kernels are set up to take
+    if (dyn > 225u * 1024u) return 0;  // the most the transform kernels are set up to take
     return dyn;
 }
 
@@ -640,11 +694,13 @@ int apply_tuning(wally_ctx *c, const wally_tuning *t)
     if (!t->max_wave) return fail(WALLY_EINVAL, "max_wave must be positive");
     if (t->lanes != 1 && t->lanes != 2) return fail(WALLY_EINVAL, "lanes must be 1 or 2");
     if (t->mac_ctas_per_sm < 1 || t->mac_ctas_per_sm > 3) return fail(WALLY_EINVAL, "mac_ctas_per_sm must be 1..3");
+    if (t->ks_core > 1) return fail(WALLY_EINVAL, "ks_core must be 0 or 1");
     c->max_wave = t->max_wave;
     c->lanes_pref = t->lanes;
     c->dp.mac_ctas_per_sm = t->mac_ctas_per_sm;
     c->ntt_cps = t->ntt_ctas_per_sm;
     c->dp.ntt_smem = ntt_smem_for(c, t->ntt_ctas_per_sm);
+    c->dp.ks_core = t->ks_core;
     return WALLY_OK;
 }
 
@@ -654,6 +710,7 @@ void current_tuning(const wally_ctx *c, wally_tuning *t)
     t->lanes = c->lanes_pref;
     t->mac_ctas_per_sm = c->dp.mac_ctas_per_sm ? c->dp.mac_ctas_per_sm : 3;
     t->ntt_ctas_per_sm = c->ntt_cps;
+    t->ks_core = c->dp.ks_core;
 }
 
 void release_waves(wally_ctx *c)
@@ -1297,6 +1354,7 @@ int wally_eval_batch_host(wally_ctx *c, uint32_t n, const uint32_t *ids, const u
         if (c->compact()) rc = encode_wave(c, ln, waves[wave], ln.zlist.p, zc.size(), st);
         if (rc == WALLY_OK) rc = run_wave(c, ln, wp, len, wave_store(c, ln), st);
         if (rc) break;
+        if (c->prof_on) c->prof.wave_end(st, len);
         CUDA_TRY(cudaEventRecord(c->comp_done[b], st));
         CUDA_TRY(cudaStreamWaitEvent(cout_, c->comp_done[b], 0));
         CUDA_TRY(cudaMemcpyAsync(c->h_out[b].p, c->stage_out[b].p, 8 * ctw * po[len], cudaMemcpyDeviceToHost, cout_));
@@ -1401,7 +1459,7 @@ int wally_autotune(wally_ctx *c, const wally_tuning *cand, uint32_t nc, uint32_t
     if (cand && !nc) return fail(WALLY_EINVAL, "no candidates");
     for (uint32_t i = 0; cand && i < nc; i++)
         if (!cand[i].max_wave || (cand[i].lanes != 1 && cand[i].lanes != 2) || cand[i].mac_ctas_per_sm < 1 ||
-            cand[i].mac_ctas_per_sm > 3)
+            cand[i].mac_ctas_per_sm > 3 || cand[i].ks_core > 1)
             return fail(WALLY_EINVAL, "invalid candidate shape %u", i);
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1430,13 +1488,19 @@ int wally_autotune(wally_ctx *c, const wally_tuning *cand, uint32_t nc, uint32_t
         for (uint32_t i = 0; i < nc && rc == WALLY_OK; i++) run(cand[i]);
     } else {
         for (uint32_t w : {512u, 1024u, 2048u})
-            for (uint32_t l : {1u, 2u}) run(wally_tuning{w, l, 3, 0});
+            for (uint32_t l : {1u, 2u}) run(wally_tuning{w, l, 3, 0, 0});
         const int b1 = best_of();
         if (rc == WALLY_OK && b1 >= 0) {
             const wally_tuning base = done[b1];
             for (uint32_t m : {2u, 3u})
                 for (uint32_t k : {0u, 2u})
-                    if (!(m == 3 && k == 0)) run(wally_tuning{base.max_wave, base.lanes, m, k});
+                    if (!(m == 3 && k == 0)) run(wally_tuning{base.max_wave, base.lanes, m, k, 0});
+        }
+        const int b2 = best_of();
+        if (rc == WALLY_OK && b2 >= 0) {
+            wally_tuning t = done[b2];
+            t.ks_core = 1;
+            run(t);
         }
     }
     cudaEventDestroy(e0);
@@ -1822,7 +1886,30 @@ int wally_profile_enable(wally_ctx *c, int enable)
     DeviceGuard guard(c->device);
     cudaDeviceSynchronize();
     c->prof.reset();
+    c->prof.reset_waves();
     c->prof_on = enable != 0;
+    return WALLY_OK;
+}
+
+int wally_profile_waves(wally_ctx *c, uint32_t cap, uint32_t *call, uint32_t *queries, float *done_ms,
+                        uint32_t *count)
+{
+    if (!c || !count) return fail(WALLY_EINVAL, "null argument");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    uint32_t n = 0;
+    for (const auto &w : c->prof.waves) {
+        if (n < cap) {
+            float t = 0;
+            CUDA_TRY(cudaEventElapsedTime(&t, c->prof.call_start[w.call], w.done));
+            if (call) call[n] = w.call;
+            if (queries) queries[n] = w.queries;
+            if (done_ms) done_ms[n] = t;
+        }
+        n++;
+    }
+    c->prof.reset_waves();
+    *count = n;
     return WALLY_OK;
 }
 

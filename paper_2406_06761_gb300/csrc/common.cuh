@@ -62,6 +62,9 @@ struct DevParams {
     // memory of the transform kernels (0 = what they need; more caps the CTAs
     // an SM holds) and resident CTAs per SM of the multiply-accumulate
     u32 ntt_smem, mac_ctas_per_sm;
+    // transform core of the key-switch kernels: 0 = shared-memory radix-16
+    // passes (three CTAs an SM), 1 = register-blocked passes (two CTAs an SM)
+    u32 ks_core;
 };
 
 __device__ __forceinline__ u64 csub(u64 x, u64 m) { return x >= m ? x - m : x; }

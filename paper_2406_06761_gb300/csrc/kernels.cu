@@ -12,6 +12,7 @@
 //   a5 output to coefficient form ............... k_output
 #include <cstdio>
 #include "kernels.hpp"
+#include "ntt_regs.cuh"
 
 namespace wally {
 
@@ -30,6 +31,16 @@ __device__ __forceinline__ u32 item_count(u32 n_max, const u32 *n_dev)
     return c < n_max ? c : n_max;
 }
 
+// Two transform cores: the register-blocked one of ntt_regs.cuh (32
+// coefficients a thread, two CTAs an SM) for the kernels that transform one
+// polynomial per CTA (inputs, outputs, chain starts), and the shared-memory
+// one of common.cuh (three CTAs an SM) for the key-switch kernels, whose
+// memory-bound phases (key inner products, ModDown) need the extra resident
+// CTAs to hide their latency.
+template <int LOGN>
+using RP = NttV<LOGN, 32>;
+#define NTT_LB(LOGN) __launch_bounds__(RP<LOGN>::T, RP<LOGN>::MIN_BLOCKS)
+
 // Shared memory of the transform kernels: one polynomial buffer and the
 // twiddle cache.
 template <int LOGN>
@@ -44,7 +55,24 @@ struct Smem {
     }
 };
 
-#define NTT_LB(LOGN) __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::MIN_BLOCKS)
+#define OLD_LB(LOGN) __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::MIN_BLOCKS)
+
+// Parameters of modulus j and the shared copies of the first 32 entries of
+// its forward and inverse twiddle tables (the register core reads the other
+// entries from global memory); ends with a barrier.
+struct ModSmem {
+    Mod md;
+    Tw twf[32], twi[32];
+};
+
+__device__ __forceinline__ void load_mod_tw(ModSmem &ms, const DevParams *dpp, int j)
+{
+    if (threadIdx.x < sizeof(Mod) / 8) ((u64 *)&ms.md)[threadIdx.x] = ((const u64 *)&dpp->m[j])[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < 32) ms.twf[threadIdx.x] = ms.md.fwd[threadIdx.x];
+    else if (threadIdx.x < 64) ms.twi[threadIdx.x - 32] = ms.md.inv[threadIdx.x - 32];
+    __syncthreads();
+}
 
 // ---------------------------------------------------------------- a1: to NTT form
 // Item x, polynomial z (modulus z % mod_cycle): forward NTT of the input
@@ -54,58 +82,84 @@ __global__ void NTT_LB(LOGN) k_to_ntt(const DevParams *dpp, const u64 *const *sr
                                       size_t src_stride, u64 *dst, size_t dst_stride, u32 mod_cycle, u32 n_max,
                                       const u32 *n_dev, bool mont)
 {
+    using P = RP<LOGN>;
     constexpr int N = 1 << LOGN;
-    extern __shared__ u64 smraw[];
-    Smem<LOGN> S(smraw);
-    __shared__ Mod md;
+    extern __shared__ u64 sm[];
+    __shared__ ModSmem ms;
     const u32 x = blockIdx.x;
     if (x >= item_count(n_max, n_dev)) return;
     const u32 z = blockIdx.y;
-    load_mod(&md, dpp, z % mod_cycle);
     const u64 *s = (src_ptrs ? src_ptrs[x] : src + x * src_stride) + (size_t)z * N;
-    u64 *d = dst + x * dst_stride + (size_t)z * N;
-    poly_load<LOGN>(S.poly, s);
-    ntt_fwd<LOGN>(S.poly, S.twf, md);
-#pragma unroll 4
-    for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = spos(e);
-        u64 a = fwd_finish(S.poly[sp], md), b = fwd_finish(S.poly[sp ^ 1], md);
-        if (mont) {
-            a = mont_mul(a, md.r2, md);
-            b = mont_mul(b, md.r2, md);
-        }
-        st2(d + e, a, b);
-    }
+    u64 v[32];
+    gload_first<P>(v, s);
+    load_mod_tw(ms, dpp, z % mod_cycle);
+    const Mod &md = ms.md;
+    ntt_fwd_v<P>(v, sm, ms.twf, md.fwd, md);
+#pragma unroll
+    for (int k = 0; k < 32; k++) v[k] = mont ? mont_mul(v[k], md.r2, md) : reduce64p(v[k], md);
+    gstore_last<P>(dst + x * dst_stride + (size_t)z * N, v);
 }
 
 // Inverse NTT, canonical coefficients.
 template <int LOGN>
 __global__ void NTT_LB(LOGN) k_from_ntt(const DevParams *dpp, const u64 *src, u64 *dst, u32 polys, u32 mod_cycle)
 {
+    using P = RP<LOGN>;
     constexpr int N = 1 << LOGN;
-    extern __shared__ u64 smraw[];
-    Smem<LOGN> S(smraw);
-    __shared__ Mod md;
+    extern __shared__ u64 sm[];
+    __shared__ ModSmem ms;
     const u32 x = blockIdx.x, z = blockIdx.y;
-    load_mod(&md, dpp, z % mod_cycle);
-    const u64 *s = src + ((size_t)x * polys + z) * N;
-    u64 *d = dst + ((size_t)x * polys + z) * N;
-    poly_load<LOGN>(S.poly, s);
-    ntt_inv<LOGN>(S.poly, S.twi, md);
-#pragma unroll 4
-    for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = spos(e);
-        st2(d + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp ^ 1], md));
-    }
+    u64 v[32];
+    gload_last<P>(v, src + ((size_t)x * polys + z) * N);
+    load_mod_tw(ms, dpp, z % mod_cycle);
+    const Mod &md = ms.md;
+    ntt_inv_v<P>(v, sm, ms.twi, md.inv, md);
+#pragma unroll
+    for (int k = 0; k < 32; k++) v[k] = inv_finish(v[k], md);
+    gstore_first<P>(dst + ((size_t)x * polys + z) * N, v);
 }
 
 // ---------------------------------------------------------------- a2/a4: rotations
-// Shared tail of k_ks_a and the fused part of k_ks_c.  The buffer holds limb
+// k_ks_a, CTA (item x, limb j, component c): first rotation of a chain.
+// Limb j of component c of the input (NTT form) is permuted by sigma_k (a
+// permutation of the evaluation positions, through shared memory) into sc;
+// for c = 1 its inverse transform gives the digit d_j = [sigma(c1)]_{q_j} in
+// [0, q_j) (reading R3: non-centred), written to dg.
+template <int LOGN>
+__global__ void NTT_LB(LOGN) k_ks_a(const DevParams *dpp, RotArgs a)
+{
+    using P = RP<LOGN>;
+    constexpr int N = 1 << LOGN;
+    extern __shared__ u64 sm[];
+    __shared__ ModSmem ms;
+    // the 2L CTAs of an item are adjacent in the grid (they share its data in L2)
+    const int L = dpp->L;
+    const u32 x = blockIdx.x / (2 * L);
+    if (x >= item_count(a.n_max, a.n_dev)) return;
+    const int y = (int)(blockIdx.x % (2 * L)), j = y % L, c = y / L;
+    u64 v[32];
+    gload_last<P>(v, a.src + x * a.src_stride + ((size_t)c * L + j) * N);
+    load_mod_tw(ms, dpp, j);
+    sm_store_last<P>(sm, v);
+    __syncthreads();
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < 32; r++) v[r] = sm[phys<P>((int)galois_src((u32)elem_last<P>(t, r), a.galois, LOGN))];
+    gstore_last<P>(a.sc + ((size_t)x * 2 * L + c * L + j) * N, v);
+    if (c == 1) {
+        ntt_inv_v<P>(v, sm, ms.twi, ms.md.inv, ms.md);
+#pragma unroll
+        for (int r = 0; r < 32; r++) v[r] = inv_finish(v[r], ms.md);
+        gstore_first<P>(a.dg + ((size_t)x * L + j) * N, v);
+    }
+}
+
+// The fused part of k_ks_c (shared-memory transform core).  The buffer holds limb
 // j of component c of a ciphertext (NTT form); write sigma_k of it to sc and,
 // for c = 1, the digit d_j = [sigma(c1)]_{q_j} in [0, q_j) (reading R3:
 // non-centred) to dg.  sigma_k is a permutation of the NTT positions.
 template <int LOGN>
-__device__ __forceinline__ void permute_and_digit(const Smem<LOGN> &S, const Mod &md, u64 k, int c, u64 *sc_cj,
+__device__ __forceinline__ void permute_and_digit_smem(const Smem<LOGN> &S, const Mod &md, u64 k, int c, u64 *sc_cj,
                                                   u64 *dg_j)
 {
     __syncthreads();
@@ -126,25 +180,6 @@ __device__ __forceinline__ void permute_and_digit(const Smem<LOGN> &S, const Mod
     }
 }
 
-// k_ks_a, CTA (item x, limb j, component c): first rotation of a chain.
-template <int LOGN>
-__global__ void NTT_LB(LOGN) k_ks_a(const DevParams *dpp, RotArgs a)
-{
-    constexpr int N = 1 << LOGN;
-    extern __shared__ u64 smraw[];
-    Smem<LOGN> S(smraw);
-    __shared__ Mod md;
-    // the 2L CTAs of an item are adjacent in the grid (they share its data in L2)
-    const int L = dpp->L;
-    const u32 x = blockIdx.x / (2 * L);
-    if (x >= item_count(a.n_max, a.n_dev)) return;
-    const int y = (int)(blockIdx.x % (2 * L)), j = y % L, c = y / L;
-    load_mod(&md, dpp, j);
-    poly_load<LOGN>(S.poly, a.src + x * a.src_stride + ((size_t)c * L + j) * N);
-    permute_and_digit<LOGN>(S, md, a.galois, c, a.sc + ((size_t)x * 2 * L + c * L + j) * N,
-                            a.dg + ((size_t)x * L + j) * N);
-}
-
 // k_ks_b, CTA (item x, modulus j in q_0..q_{L-1}, P):
 //   u_j = sum_i NTT_j(d_i) * key_{i,j}  for both key components,
 // as one lazy 128-bit sum per output and a single Montgomery reduction (the
@@ -152,7 +187,7 @@ __global__ void NTT_LB(LOGN) k_ks_a(const DevParams *dpp, RotArgs a)
 // other digits are transformed here, all but the last one parked in dd.  For
 // j = P the sums are brought back to coefficients (r = [u]_P) for ModDown.
 template <int LOGN>
-__global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
+__global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
 {
     constexpr int N = 1 << LOGN;
     extern __shared__ u64 smraw[];
@@ -236,7 +271,7 @@ __global__ void NTT_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
 // With next_galois set, the output is also prepared as the input of the next
 // rotation of the chain (its automorphism and, for c = 1, its digit).
 template <int LOGN>
-__global__ void NTT_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
+__global__ void OLD_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
 {
     constexpr int N = 1 << LOGN;
     extern __shared__ u64 smraw[];
@@ -286,7 +321,143 @@ __global__ void NTT_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
         S.poly[sp ^ 1] = v1;
     }
     if (a.next_galois)
-        permute_and_digit<LOGN>(S, md, a.next_galois, c, sc_cj, a.dg + ((size_t)x * L + j) * N);
+        permute_and_digit_smem<LOGN>(S, md, a.next_galois, c, sc_cj, a.dg + ((size_t)x * L + j) * N);
+}
+
+// The same two key-switch kernels on the register core (two CTAs an SM): the
+// digits' transforms read their input straight into registers and leave
+// the evaluations there for the inner product, and ModDown's transform
+// feeds the pointwise step without a pass through shared memory.
+template <int LOGN>
+__global__ void NTT_LB(LOGN) k_ks_b_reg(const DevParams *dpp, RotArgs a)
+{
+    using P = RP<LOGN>;
+    constexpr int N = 1 << LOGN;
+    extern __shared__ u64 sm[];
+    __shared__ ModSmem ms;
+    const int L = dpp->L;
+    const u32 x = blockIdx.x / (L + 1);
+    if (x >= item_count(a.n_max, a.n_dev)) return;
+    const int j = L - (int)(blockIdx.x % (L + 1));
+    const int last = (j == L - 1) ? L - 2 : L - 1;
+    u64 v[32];
+    const int i0 = (j == 0) ? 1 : 0;
+    if (i0 < L) gload_first<P>(v, a.dg + ((size_t)x * L + i0) * N);
+    load_mod_tw(ms, dpp, j);
+    for (int i = i0; i < L; i++) {
+        if (i == j) continue;
+        if (i != i0) gload_first<P>(v, a.dg + ((size_t)x * L + i) * N);  // < q_i < 2 p_j
+        ntt_fwd_v<P>(v, sm, ms.twf, ms.md.fwd, ms.md);                 // lazy, < 56 p_j
+        if (i != last) gstore_last<P>(a.dd + (((size_t)x * (L + 1) + j) * L + i) * N, v);
+    }
+    const Mod &md = ms.md;
+    const u64 *kx = a.key + (size_t)(a.key_map ? a.key_map[x] : x) * a.key_stride;
+    const u64 *dd = a.dd + ((size_t)x * (L + 1) + j) * L * N;
+    u64 *u0 = a.u + ((size_t)x * 2 + 0) * (L + 1) * N + (size_t)j * N;
+    u64 *u1 = a.u + ((size_t)x * 2 + 1) * (L + 1) * N + (size_t)j * N;
+    const u64 *sc1 = a.sc + ((size_t)x * 2 * L + L + j) * N;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 32; k += 2) {
+        const int e = elem_last<P>(t, k);
+        u64 h0a = 0, l0a = 0, h0b = 0, l0b = 0, h1a = 0, l1a = 0, h1b = 0, l1b = 0;
+        for (int i = 0; i < L; i++) {
+            u64 da, db;
+            if (i == j) {
+                const ulonglong2 q = ld2(sc1 + e);
+                da = q.x;
+                db = q.y;
+            } else if (i == last) {
+                da = v[k];
+                db = v[k + 1];
+            } else {
+                const ulonglong2 q = ld2(dd + (size_t)i * N + e);  // this thread's own writes
+                da = q.x;
+                db = q.y;
+            }
+            const ulonglong2 kb = ldg2(kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N + e);
+            const ulonglong2 ka = ldg2(kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N + e);
+            mac128(h0a, l0a, da, kb.x);
+            mac128(h0b, l0b, db, kb.y);
+            mac128(h1a, l1a, da, ka.x);
+            mac128(h1b, l1b, db, ka.y);
+        }
+        st2(u0 + e, mont_redc(h0a, l0a, md), mont_redc(h0b, l0b, md));
+        st2(u1 + e, mont_redc(h1a, l1a, md), mont_redc(h1b, l1b, md));
+    }
+    if (j == L) {
+        for (int c = 0; c < 2; c++) {
+            u64 *uc = c ? u1 : u0;
+            gload_last<P, true>(v, uc);  // this thread's own writes
+            ntt_inv_v<P>(v, sm, ms.twi, md.inv, md);
+#pragma unroll
+            for (int k = 0; k < 32; k++) v[k] = inv_finish(v[k], md);
+            gstore_first<P>(uc, v);
+        }
+    }
+}
+
+template <int LOGN>
+__global__ void NTT_LB(LOGN) k_ks_c_reg(const DevParams *dpp, RotArgs a)
+{
+    using P = RP<LOGN>;
+    constexpr int N = 1 << LOGN;
+    extern __shared__ u64 sm[];
+    __shared__ ModSmem ms;
+    const int L = dpp->L;
+    const u32 x = blockIdx.x / (2 * L);
+    if (x >= item_count(a.n_max, a.n_dev)) return;
+    const int y = (int)(blockIdx.x % (2 * L)), j = y % L, c = 1 - y / L;
+    u64 v[32];
+    gload_first<P>(v, a.u + (((size_t)x * 2 + c) * (L + 1) + L) * N);  // r = [u]_P, coefficients
+    load_mod_tw(ms, dpp, j);
+    const Mod &md = ms.md;
+    const u64 q = md.p, Pm = dpp->m[L].p, half = (Pm - 1) / 2;
+    const u64 pinv = dpp->pinv[j], pinv_s = dpp->pinv_s[j];
+#pragma unroll
+    for (int k = 0; k < 32; k++) v[k] = v[k] > half ? q - (Pm - v[k]) : v[k];  // r_c mod q_j, < 2q
+    ntt_fwd_v<P>(v, sm, ms.twf, md.fwd, md);  // < 58q
+    const u64 *uj = a.u + (((size_t)x * 2 + c) * (L + 1) + j) * N;
+    u64 *sc_cj = a.sc + ((size_t)x * 2 * L + c * L + j) * N;
+    const u64 *ad = a.add ? a.add + x * a.add_stride + ((size_t)c * L + j) * N : nullptr;
+    u64 *dst = a.dst + x * a.dst_stride + ((size_t)c * L + j) * N;
+    const u64 q64 = q << 6;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 32; k += 2) {
+        const int e = elem_last<P>(t, k);
+        const ulonglong2 uv = ldg2(uj + e);
+        u64 v0 = csub(shoup_mul(uv.x + q64 - v[k], pinv, pinv_s, q), q);
+        u64 v1 = csub(shoup_mul(uv.y + q64 - v[k + 1], pinv, pinv_s, q), q);
+        if (c == 0) {
+            const ulonglong2 s0 = ld2(sc_cj + e);
+            v0 = addmod(v0, s0.x, q);
+            v1 = addmod(v1, s0.y, q);
+        }
+        if (ad) {
+            const ulonglong2 tt = ldg2(ad + e);
+            v0 = addmod(v0, tt.x, q);
+            v1 = addmod(v1, tt.y, q);
+        }
+        v[k] = v0;
+        v[k + 1] = v1;
+    }
+    gstore_last<P>(dst, v);
+    if (a.next_galois) {
+        __syncthreads();  // every thread has read sigma(c0) from sc_cj before it is replaced
+        sm_store_last<P>(sm, v);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 32; r++)
+            v[r] = sm[phys<P>((int)galois_src((u32)elem_last<P>(t, r), a.next_galois, LOGN))];
+        gstore_last<P>(sc_cj, v);
+        if (c == 1) {
+            ntt_inv_v<P>(v, sm, ms.twi, md.inv, md);
+#pragma unroll
+            for (int r = 0; r < 32; r++) v[r] = inv_finish(v[r], md);
+            gstore_first<P>(a.dg + ((size_t)x * L + j) * N, v);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- a3: PtCt products
@@ -422,24 +593,21 @@ __global__ void __launch_bounds__(256) k_mac_wide(const DevParams *dpp, ClusterS
 template <int LOGN>
 __global__ void NTT_LB(LOGN) k_output(const DevParams *dpp, WavePlan wp, const u64 *S_, size_t S_stride, u32 n_max)
 {
+    using P = RP<LOGN>;
     constexpr int N = 1 << LOGN;
-    extern __shared__ u64 smraw[];
-    Smem<LOGN> S(smraw);
-    __shared__ Mod md;
+    extern __shared__ u64 sm[];
+    __shared__ ModSmem ms;
     const u32 p = blockIdx.x;
     if (p >= item_count(n_max, wp.counts + 1)) return;
     const int L = dpp->L;
     const int z = blockIdx.y, l = z % L;
-    load_mod(&md, dpp, l);
-    const u64 *s = S_ + p * S_stride + (size_t)z * N;
-    u64 *d = wp.dst_out[wp.pair_pos[p]] + (size_t)wp.pair_k[p] * 2 * L * N + (size_t)z * N;
-    poly_load<LOGN>(S.poly, s);
-    ntt_inv<LOGN>(S.poly, S.twi, md);
-#pragma unroll 4
-    for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = spos(e);
-        st2(d + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp ^ 1], md));
-    }
+    u64 v[32];
+    gload_last<P>(v, S_ + p * S_stride + (size_t)z * N);
+    load_mod_tw(ms, dpp, l);
+    ntt_inv_v<P>(v, sm, ms.twi, ms.md.inv, ms.md);
+#pragma unroll
+    for (int k = 0; k < 32; k++) v[k] = inv_finish(v[k], ms.md);
+    gstore_first<P>(wp.dst_out[wp.pair_pos[p]] + (size_t)wp.pair_k[p] * 2 * L * N + (size_t)z * N, v);
 }
 
 // ---------------------------------------------------------------- a0: grouping
@@ -560,9 +728,9 @@ cudaError_t set_smem(K kernel, size_t bytes)
 }
 
 // the transform kernels may be launched with more shared memory than they
-// use (fewer CTAs per SM): up to 226 KB, which with their static shared
+// use (fewer CTAs per SM): up to 225 KB, which with their static shared
 // memory stays within the 227 KB a CTA may opt in to
-constexpr size_t kMaxDynSmem = 226 * 1024;
+constexpr size_t kMaxDynSmem = 225 * 1024;
 
 template <int LOGN>
 cudaError_t set_attrs_logn()
@@ -575,6 +743,8 @@ cudaError_t set_attrs_logn()
     SA(k_ks_a);
     SA(k_ks_b);
     SA(k_ks_c);
+    SA(k_ks_b_reg);
+    SA(k_ks_c_reg);
     SA(k_output);
 #undef SA
     return e;
@@ -591,7 +761,8 @@ cudaError_t set_attrs_logn()
     }
 
 // dynamic shared memory of a transform kernel: its need, or the tuned size
-#define SMEM(LG) (dp.ntt_smem > ntt_smem_words<LG>() * 8 ? (size_t)dp.ntt_smem : (size_t)ntt_smem_words<LG>() * 8)
+#define SMEM(LG) (dp.ntt_smem > (8u << LG) ? (size_t)dp.ntt_smem : (size_t)8 << LG)
+#define SMEM_OLD(LG) (dp.ntt_smem > ntt_smem_words<LG>() * 8 ? (size_t)dp.ntt_smem : (size_t)ntt_smem_words<LG>() * 8)
 static inline int ntt_threads(int log_n) { return (1 << log_n) / 32; }
 
 cudaError_t set_client_kernel_attributes(int log_n);
@@ -671,13 +842,20 @@ cudaError_t launch_rotate(const DevParams &dp, const RotArgs &a, cudaStream_t st
                           ProfScope ps(pr, KK_KS_A, st);
                           k_ks_a<LG><<<a.n_max * 2 * L, ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
                       }
-                      {
-                          ProfScope ps(pr, KK_KS_B, st);
-                          k_ks_b<LG><<<a.n_max * (L + 1), ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
-                      }
-                      {
+                      if (dp.ks_core == 1) {
+                          {
+                              ProfScope ps(pr, KK_KS_B, st);
+                              k_ks_b_reg<LG><<<a.n_max * (L + 1), ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
+                          }
                           ProfScope ps(pr, KK_KS_C, st);
-                          k_ks_c<LG><<<a.n_max * 2 * L, ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
+                          k_ks_c_reg<LG><<<a.n_max * 2 * L, ntt_threads(LG), SMEM(LG), st>>>(dpp, a);
+                      } else {
+                          {
+                              ProfScope ps(pr, KK_KS_B, st);
+                              k_ks_b<LG><<<a.n_max * (L + 1), ntt_threads(LG), SMEM_OLD(LG), st>>>(dpp, a);
+                          }
+                          ProfScope ps(pr, KK_KS_C, st);
+                          k_ks_c<LG><<<a.n_max * 2 * L, ntt_threads(LG), SMEM_OLD(LG), st>>>(dpp, a);
                       }
                   }));
     return cudaGetLastError();

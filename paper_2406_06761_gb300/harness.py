@@ -32,9 +32,18 @@ class Pool:
 
 
 class DeviceWorkload:
+    """shard = (world, rank): load only the clusters this rank owns (cluster
+    shards balanced by chunks x expected queries, multigpu.shard_clusters) and
+    take, out of `world` batches of the workload (seeds seed .. seed+world-1),
+    the queries that name them, with local cluster ids; every rank then
+    evaluates about one batch (weak scaling) and no query is evaluated
+    twice."""
+
     def __init__(self, name: str, seed: int = 0, device: int = 0, pool: int | None = None, max_wave: int = 0,
                  real_queries: int | None = None, num_clusters: int | None = None, sizes=None,
-                 keep_embeddings: bool = True, verbose: bool = False, **ctx_kw):
+                 keep_embeddings: bool = True, verbose: bool = False, shard: tuple[int, int] | None = None,
+                 **ctx_kw):
+        from . import multigpu as M
         w = W.WORKLOADS[name]
         if real_queries is not None or num_clusters is not None:
             w = dataclasses.replace(w, real_queries=real_queries if real_queries is not None else w.real_queries,
@@ -45,16 +54,33 @@ class DeviceWorkload:
         info = self.ctx.info
         self.N, self.L, self.q, self.P = info.n, info.num_q, self.ctx.q, self.ctx.P
         self.ctw, self.keysw = int(info.ct_words), int(info.keys_words)
-        self.sizes = np.asarray(sizes if sizes is not None else W.cluster_sizes(w, seed), dtype=np.int64)
+        sizes_all = np.asarray(sizes if sizes is not None else W.cluster_sizes(w, seed), dtype=np.int64)
+        emb_all = W.embeddings(int(sizes_all.sum()), w.dim, w.entry_bound, seed)
+        self.shard = shard
+        if shard is None:
+            self.sizes, emb = sizes_all, emb_all
+            self.ids, self.is_real = W.query_mix(w, self.sizes, seed)
+            self.global_clusters = np.arange(len(sizes_all))
+        else:
+            world, rank = shard
+            mixes = [W.query_mix(w, sizes_all, seed + b) for b in range(world)]
+            ids_all = np.concatenate([m[0] for m in mixes])
+            real_all = np.concatenate([m[1] for m in mixes])
+            chunks_all = np.maximum(1, -(-sizes_all // self.N))
+            owner = M.shard_clusters(chunks_all, np.bincount(ids_all, minlength=len(sizes_all)), world)
+            self.global_clusters = M.local_clusters(owner, rank)
+            mine, local_ids = M.route(ids_all, owner, rank)
+            self.ids, self.is_real = local_ids, real_all[mine]
+            self.sizes = sizes_all[self.global_clusters]
+            row0_all = np.concatenate([[0], np.cumsum(sizes_all)[:-1]])
+            emb = np.concatenate([emb_all[row0_all[c]:row0_all[c] + sizes_all[c]] for c in self.global_clusters])
         total = int(self.sizes.sum())
-        emb = W.embeddings(total, w.dim, w.entry_bound, seed)
         self._log(f"load {len(self.sizes)} clusters, {total} embeddings")
         Wl.wally_load_clusters(self.ctx.ptr, self.sizes.astype(np.uint32), emb)
         self.ctx.refresh()
         self.embeddings = emb if keep_embeddings else None
         self.row0 = np.concatenate([[0], np.cumsum(self.sizes)[:-1]]).astype(np.int64)
         self.chunks = np.array([Wl.wally_cluster_chunks(self.ctx.ptr, c) for c in range(len(self.sizes))], np.int64)
-        self.ids, self.is_real = W.query_mix(w, self.sizes, seed)
         self.n = len(self.ids)
         self.pool_size = int(pool) if pool else self.n
         self._build_pool()

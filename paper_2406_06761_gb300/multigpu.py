@@ -9,7 +9,8 @@ Two placements:
   copy of a batch);
 - cluster shards: every rank holds a subset of the clusters, chosen to
   balance chunks x expected queries, and the host routes each query to the
-  rank that owns its cluster.
+  rank that owns its cluster (harness.DeviceWorkload(shard=...) builds a
+  rank's share; bench.py uses it under torchrun).
 
 Only timing crosses ranks: a barrier and the maximum of the step times.
 """
@@ -63,6 +64,17 @@ def max_over_ranks(value: float, device=None) -> float:
         return float(value)
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, device=None) -> float:
+    """Sum of a scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 

@@ -33,29 +33,48 @@ from . import wally as Wl
 
 @dataclasses.dataclass
 class Stream:
-    """A request stream: arrival time (s), cluster id, submission index."""
+    """A request stream: arrival time (s), cluster id, submission index, and
+    (optionally) the client each request came from."""
     arrival: np.ndarray
     cluster: np.ndarray
     entry: np.ndarray
     is_real: np.ndarray
+    client: np.ndarray | None = None
 
 
-def poisson_stream(rate_qps: float, seconds: float, sizes, n_entries: int, fake_fraction: float,
+def poisson_stream(rate_qps: float, seconds: float, sizes, n_entries: int, nb_r: float = 0.5, nb_p: float = 0.9,
                    seed: int = 0) -> Stream:
-    """Poisson arrivals at `rate_qps` (real and fake queries together) for
-    `seconds`: real queries pick clusters in proportion to size, fakes
-    uniformly; submissions cycle over the pool (fakes over its last part)."""
+    """The anonymised request stream over `seconds` at an offered rate of
+    `rate_qps` real and fake queries together.  Clients follow Alg. "Client
+    Query Generation": each sends one real query, on a cluster drawn in
+    proportion to cluster size, and NB(nb_r, nb_p) fake queries (numpy's
+    convention, the per-client count of the workload generator) on uniform
+    clusters; every query is sent at its own uniform time (Alg. "Schedule"
+    gives each query an independent random slot), so the arrivals form a
+    Poisson process.  The number of clients is Poisson with mean
+    rate * seconds / (1 + E[fakes]).  Submissions cycle over the pool: real
+    queries over its first entries, fakes over the last ones (in proportion
+    to the expected fake share, at least one)."""
+    from . import workload as W
     rng = np.random.default_rng([seed, 0x5e4])
-    n = max(1, int(rng.poisson(rate_qps * seconds)))
-    arrival = np.sort(rng.uniform(0.0, seconds, size=n))
-    is_real = rng.uniform(size=n) >= fake_fraction
+    mean_fakes = nb_r * (1.0 - nb_p) / nb_p if nb_r > 0 else 0.0
+    n_clients = max(1, int(rng.poisson(rate_qps * seconds / (1.0 + mean_fakes))))
+    fakes = W.fake_counts(n_clients, nb_r, nb_p, seed=seed + 0x5e4)
+    client = np.concatenate([np.arange(n_clients), np.repeat(np.arange(n_clients), fakes)])
+    is_real = np.concatenate([np.ones(n_clients, bool), np.zeros(int(fakes.sum()), bool)])
+    n = len(client)
     p = np.asarray(sizes, dtype=np.float64)
     cluster = np.where(is_real, rng.choice(len(p), size=n, p=p / p.sum()), rng.integers(0, len(p), size=n))
-    n_fake_entries = max(1, int(round(n_entries * fake_fraction))) if fake_fraction > 0 else 0
+    arrival = rng.uniform(0.0, seconds, size=n)
+    order = np.argsort(arrival, kind="stable")
+    arrival, client, is_real, cluster = arrival[order], client[order], is_real[order], cluster[order]
+    share = mean_fakes / (1.0 + mean_fakes)
+    n_fake_entries = max(1, int(round(n_entries * share))) if share > 0 else 0
+    n_fake_entries = min(n_fake_entries, max(0, n_entries - 1))
     n_real_entries = n_entries - n_fake_entries
-    entry = np.where(is_real, np.arange(n) % max(1, n_real_entries),
-                     n_real_entries + np.arange(n) % max(1, n_fake_entries))
-    return Stream(arrival, cluster.astype(np.uint32), entry.astype(np.uint32), is_real)
+    k = np.arange(n)
+    entry = np.where(is_real, k % max(1, n_real_entries), n_real_entries + k % max(1, n_fake_entries))
+    return Stream(arrival, cluster.astype(np.uint32), entry.astype(np.uint32), is_real, client.astype(np.int64))
 
 
 class _Lane:

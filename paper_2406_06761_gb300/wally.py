@@ -51,7 +51,7 @@ class wally_info(ctypes.Structure):
 
 class wally_tuning(ctypes.Structure):
     _fields_ = [("max_wave", ctypes.c_uint32), ("lanes", ctypes.c_uint32), ("mac_ctas_per_sm", ctypes.c_uint32),
-                ("ntt_ctas_per_sm", ctypes.c_uint32)]
+                ("ntt_ctas_per_sm", ctypes.c_uint32), ("ks_core", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -89,6 +89,8 @@ SIGNATURES = {
     "wally_decrypt_compressed": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "wally_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "wally_profile_read": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_u32)]),
+    "wally_profile_waves": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, ctypes.POINTER(_u32)]),
+    "wally_measure_pipe_rates": (ctypes.c_int, [ctypes.c_int32, _vp]),
     "wally_measure_int_peaks": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "wally_pir_load": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp]),
@@ -290,10 +292,32 @@ def wally_profile_read(ctx: int) -> dict:
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(cnt.value)}
 
 
+def wally_profile_waves(ctx: int, cap: int = 1 << 16):
+    """Wave completions since profiling was enabled: (call, queries, done_ms)
+    numpy arrays, one entry per wave in submission order."""
+    import numpy as np
+    call = np.zeros(cap, np.uint32)
+    q = np.zeros(cap, np.uint32)
+    ms = np.zeros(cap, np.float32)
+    cnt = _u32()
+    _check(load().wally_profile_waves(ctx, cap, call.ctypes.data, q.ctypes.data, ms.ctypes.data, ctypes.byref(cnt)))
+    n = min(cap, cnt.value)
+    return call[:n], q[:n], ms[:n]
+
+
 def wally_measure_int_peaks(device: int = 0) -> dict:
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().wally_measure_int_peaks(device, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return {"modmul_per_s": a.value, "butterfly_per_s": b.value, "mac128_per_s": c.value}
+
+
+def wally_measure_pipe_rates(device: int = 0) -> dict:
+    """Issue rates of the 32-bit multiply instructions, the SM clock, and
+    the NTT butterfly's multiplier ceiling (operations per second, Hz)."""
+    arr = (ctypes.c_double * 5)()
+    _check(load().wally_measure_pipe_rates(device, ctypes.cast(arr, _vp)))
+    names = ("mad_lo_per_s", "mul_hi_per_s", "mad_wide_per_s", "sm_clock_hz", "bfly_ceiling_per_s")
+    return dict(zip(names, (float(x) for x in arr)))
 
 
 def wally_pir_load(ctx: int, table, stream=None) -> None:
@@ -356,8 +380,8 @@ def wally_get_tuning(ctx: int) -> wally_tuning:
 
 
 def wally_set_tuning(ctx: int, max_wave: int, lanes: int = 2, mac_ctas_per_sm: int = 3,
-                     ntt_ctas_per_sm: int = 0) -> None:
-    t = wally_tuning(max_wave, lanes, mac_ctas_per_sm, ntt_ctas_per_sm)
+                     ntt_ctas_per_sm: int = 0, ks_core: int = 0) -> None:
+    t = wally_tuning(max_wave, lanes, mac_ctas_per_sm, ntt_ctas_per_sm, ks_core)
     _check(load().wally_set_tuning(ctx, ctypes.byref(t)))
 
 

@@ -27,10 +27,10 @@ def _run(wl, batch):
 
 
 SHAPES = [
-    dict(max_wave=256, lanes=2, mac_ctas_per_sm=3, ntt_ctas_per_sm=0),
-    dict(max_wave=100, lanes=1, mac_ctas_per_sm=1, ntt_ctas_per_sm=1),
-    dict(max_wave=333, lanes=2, mac_ctas_per_sm=2, ntt_ctas_per_sm=2),
-    dict(max_wave=2048, lanes=1, mac_ctas_per_sm=3, ntt_ctas_per_sm=3),
+    dict(max_wave=256, lanes=2, mac_ctas_per_sm=3, ntt_ctas_per_sm=0, ks_core=0),
+    dict(max_wave=100, lanes=1, mac_ctas_per_sm=1, ntt_ctas_per_sm=1, ks_core=1),
+    dict(max_wave=333, lanes=2, mac_ctas_per_sm=2, ntt_ctas_per_sm=2, ks_core=0),
+    dict(max_wave=2048, lanes=1, mac_ctas_per_sm=3, ntt_ctas_per_sm=3, ks_core=1),
 ]
 
 
@@ -64,7 +64,7 @@ def test_autotune_skips_a_shape_that_does_not_fit(wl):
     batch = wl.device_batch(0, 64)
     ids, idx, offs, chunks, _ = batch
     out = wl.alloc_out(chunks)
-    huge = dict(max_wave=1 << 22, lanes=2, mac_ctas_per_sm=3, ntt_ctas_per_sm=0)  # ~100 TB of workspace
+    huge = dict(max_wave=1 << 22, lanes=2, mac_ctas_per_sm=3, ntt_ctas_per_sm=0, ks_core=0)  # ~100 TB of workspace
     best, table = Wl.wally_autotune(wl.ctx.ptr, ids.numel(), ids, wl.pool.cts, wl.pool.keys, idx, offs, out,
                                     candidates=[huge, SHAPES[0]], reps=1)
     assert table[0][1] == -1 and table[1][1] > 0 and best == 1
@@ -72,7 +72,8 @@ def test_autotune_skips_a_shape_that_does_not_fit(wl):
 
 
 def test_invalid_shapes_are_rejected(wl):
-    for bad in (dict(max_wave=0), dict(max_wave=8, lanes=3), dict(max_wave=8, mac_ctas_per_sm=4)):
+    for bad in (dict(max_wave=0), dict(max_wave=8, lanes=3), dict(max_wave=8, mac_ctas_per_sm=4),
+                dict(max_wave=8, ks_core=2)):
         with pytest.raises(Wl.WallyError) as e:
             Wl.wally_set_tuning(wl.ctx.ptr, **bad)
         assert e.value.code == Wl.WALLY_EINVAL
@@ -80,18 +81,23 @@ def test_invalid_shapes_are_rejected(wl):
 
 def test_staged_search(wl):
     """Without candidates: wave size x lanes first, then the CTA counts at the
-    best of those; the kept shape is the fastest timed."""
+    best of those, then the other NTT shape of the key-switch kernels at the
+    best so far; the kept shape is the fastest timed."""
     batch = wl.device_batch(0, wl.n)
     ids, idx, offs, chunks, _ = batch
     out = wl.alloc_out(chunks)
     best, table = Wl.wally_autotune(wl.ctx.ptr, ids.numel(), ids, wl.pool.cts, wl.pool.keys, idx, offs, out, reps=1)
-    assert len(table) == 9
+    assert len(table) == 10
     first = table[:6]
     assert sorted((s["max_wave"], s["lanes"]) for s, _ in first) == [(w, l) for w in (512, 1024, 2048) for l in (1, 2)]
     ok = [m for _, m in first if m > 0]
     s1 = first[[m for _, m in first].index(min(ok))][0]
     for s, _ in table[6:]:
         assert (s["max_wave"], s["lanes"]) == (s1["max_wave"], s1["lanes"])
+    assert all(s["ks_core"] == 0 for s, _ in table[:9]) and table[9][0]["ks_core"] == 1
+    ms9 = [m if m > 0 else float("inf") for _, m in table[:9]]
+    s2 = table[int(np.argmin(ms9))][0]
+    assert dict(table[9][0], ks_core=0) == s2
     ms = [m if m > 0 else float("inf") for _, m in table]
     assert best == int(np.argmin(ms))
     assert Wl.wally_get_tuning(wl.ctx.ptr).as_dict() == table[best][0]

@@ -201,3 +201,71 @@ def test_eval_batch_captured_in_a_cuda_graph():
         assert torch.equal(out, ref)
     Wl.wally_sync(wl.ctx.ptr)
     wl.close()
+
+
+def test_wave_records_and_profiling_under_graph_replay():
+    """wally_profile_waves: one record per wave, queries summing to the batch,
+    times increasing within a lane's stream order; launches captured in a CUDA
+    graph with profiling on are timed by each replay (same launch count as the
+    plain call, positive times)."""
+    wl = H.DeviceWorkload("batched", max_wave=256)
+    b = wl.device_batch(0, wl.n)
+    out = wl.alloc_out(b[3])
+    wl.eval(b, out)
+    Wl.wally_sync(wl.ctx.ptr)
+    Wl.wally_profile_enable(wl.ctx.ptr, True)
+    wl.eval(b, out)
+    call, q, ms = Wl.wally_profile_waves(wl.ctx.ptr)
+    plain = Wl.wally_profile_read(wl.ctx.ptr)
+    Wl.wally_profile_enable(wl.ctx.ptr, False)
+    assert len(q) == -(-wl.n // 256) and int(q.sum()) == wl.n and set(call.tolist()) == {0}
+    assert np.all(ms > 0)
+    assert np.all(np.diff(ms[0::2]) > 0) and np.all(np.diff(ms[1::2]) > 0)  # each lane's waves in order
+    Wl.wally_profile_enable(wl.ctx.ptr, True)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        wl.eval(b, out)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    call2, q2, ms2 = Wl.wally_profile_waves(wl.ctx.ptr)
+    graphed = Wl.wally_profile_read(wl.ctx.ptr)
+    Wl.wally_profile_enable(wl.ctx.ptr, False)
+    del g
+    assert {k: v[0] for k, v in graphed.items()} == {k: v[0] for k, v in plain.items()}
+    assert all(v[1] > 0 for v in graphed.values())
+    assert int(q2.sum()) == wl.n and np.all(ms2 > 0)
+    wl.close()
+
+
+def test_two_cluster_shards_match_a_context_with_every_cluster():
+    """Cluster sharding on one GPU as two logical shards: each shard's context
+    holds only the clusters it owns and evaluates the queries routed to it
+    (local cluster ids) out of two batches of the workload.  The shards
+    together take every query exactly once, and each query's outputs equal
+    those of a context holding every cluster (global ids, same submission)."""
+    from paper_2406_06761_gb300 import multigpu as M
+    world = 2
+    kw = dict(num_clusters=12, real_queries=150, pool=24, max_wave=64, keep_embeddings=False)
+    shards = [H.DeviceWorkload("batched", shard=(world, r), **kw) for r in range(world)]
+    full = H.DeviceWorkload("batched", **kw)
+    # routing: disjoint owned clusters, every query of both batches once
+    owned = np.concatenate([s.global_clusters for s in shards])
+    assert sorted(owned.tolist()) == list(range(len(full.sizes)))
+    mixes = [W.query_mix(full.w, full.sizes, b) for b in range(world)]
+    assert sum(s.n for s in shards) == sum(len(m[0]) for m in mixes)
+    for s in shards:
+        b = s.device_batch(0, s.n)
+        out = s.alloc_out(b[3])
+        s.eval(b, out)
+        Wl.wally_sync(s.ctx.ptr)
+        gids = torch.from_numpy(s.global_clusters[s.ids].astype(np.int32)).to(out.device)
+        ref = full.alloc_out(b[3])
+        Wl.wally_eval_batch(full.ctx.ptr, s.n, gids, s.pool.cts, s.pool.keys, b[1], b[2], ref)
+        Wl.wally_sync(full.ctx.ptr)
+        assert torch.equal(out, ref)
+        assert np.array_equal(full.chunks[s.global_clusters], s.chunks)
+    for s in shards:
+        s.close()
+    full.close()

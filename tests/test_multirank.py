@@ -67,6 +67,7 @@ def _worker(rank, world, port, mode, out_q):
     gathered = [None] * world
     dist.all_gather_object(gathered, res)
     tmax = M.max_over_ranks(float(rank + 1))
+    tsum = M.sum_over_ranks(float(rank + 1))
     if rank == 0:
         merged = {}
         for g in gathered:
@@ -77,7 +78,7 @@ def _worker(rank, world, port, mode, out_q):
         for q in range(len(ids)):
             m = clusters[ids[q]][0]
             ok = ok and merged[q] == full[int(offs[q]):int(offs[q]) + m].tolist()
-        out_q.put((ok, tmax))
+        out_q.put((ok, tmax, tsum))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -90,12 +91,12 @@ def test_two_ranks_partition_and_agree(mode):
     procs = [ctx.Process(target=_worker, args=(r, 2, port, mode, q)) for r in range(2)]
     for p in procs:
         p.start()
-    ok, tmax = q.get(timeout=300)
+    ok, tmax, tsum = q.get(timeout=300)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
     assert ok
-    assert tmax == 2.0
+    assert tmax == 2.0 and tsum == 3.0
 
 
 def test_shard_balance_and_split():
@@ -106,4 +107,4 @@ def test_shard_balance_and_split():
     assert spans == [(0, 4), (4, 7), (7, 10)]
     mine, local = M.route(np.array([3, 0, 3, 1]), np.array([0, 1, 1, 0]), 1)
     assert list(mine) == [3] and list(local) == [0]   # query 3 names cluster 1, owned by rank 1
-    assert M.max_over_ranks(3.5) == 3.5
+    assert M.max_over_ranks(3.5) == 3.5 and M.sum_over_ranks(2.5) == 2.5

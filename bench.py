@@ -95,7 +95,7 @@ class ClockSampler:
 # ---------------------------------------------------------------- recorded ncu traffic
 
 KERNEL_SOURCES = ["paper_2406_06761_gb300/csrc/kernels.cu", "paper_2406_06761_gb300/csrc/common.cuh",
-                  "paper_2406_06761_gb300/csrc/kernels.hpp"]
+                  "paper_2406_06761_gb300/csrc/kernels.hpp", "paper_2406_06761_gb300/csrc/ntt_regs.cuh"]
 
 
 def kernel_source_hash() -> str:
@@ -109,24 +109,27 @@ def kernel_source_hash() -> str:
 
 def recorded_traffic(kernel: str, items_per_launch: float | None = None):
     """DRAM bytes per launch of `kernel` from the committed ncu summary in
-    profiles/ (a launch of 1,024 items), scaled to `items_per_launch` items
-    (the key-switch kernels' traffic grows in proportion to the items), or
-    None when that capture was taken on other kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}_1024_items.md")
-    if not os.path.exists(path):
-        return None
-    fields = {}
-    for line in open(path):
-        if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
-            fields[k.strip()] = v.strip().strip("`")
-    if fields.get("kernel_source_sha256") != kernel_source_hash():
-        return None
-    try:
-        b = float(fields["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
-    return b if items_per_launch is None else b / 1024.0 * items_per_launch
+    profiles/ (`ncu_<kernel>_<items>_items.md`, a launch of that many items
+    of a small case), scaled to `items_per_launch` items (the key-switch
+    kernels' traffic grows in proportion to the items), or None when no
+    capture exists or it was taken on other kernel sources."""
+    import glob
+    paths = sorted(glob.glob(os.path.join(ROOT, "profiles", f"ncu_{kernel}_*_items.md")))
+    for path in paths:
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel_source_sha256") != kernel_source_hash():
+            continue
+        try:
+            b = float(fields["dram_bytes_per_launch"])
+            items = float(fields["items_per_launch"])
+        except (KeyError, ValueError):
+            continue
+        return b if items_per_launch is None else b / items * items_per_launch
+    return None
 
 
 # ---------------------------------------------------------------- algorithmic work
@@ -580,7 +583,7 @@ def main():
                 "work": {k: float(v) for k, v in work[dom].items()},
                 "traffic": recorded_traffic(dom, ks_count / max(1, kern[dom]["launches"] * (args.steps if use_graph else 1))
                                            if dom.startswith("ks_") else None),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1,024-item launch "
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of a small case "
                                   "(profiles/), scaled to this run's mean items per launch",
                 "peak_source": "measured: wally_measure_int_peaks (the transforms' forward butterfly in registers, "
                                "all SMs, this GPU); Shoup products and 128-bit multiply-accumulates counted as "

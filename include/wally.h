@@ -416,19 +416,24 @@ int wally_measure_pipe_rates(int32_t device, wally_pipe_rates *out);
  *                    polynomial, 16 coefficients a thread at a time, three
  *                    CTAs an SM; 1 = passes of 5 + 5 + 3 stages on 32
  *                    coefficients held in registers, two CTAs an SM
- * Defaults: 1024 (or the max_wave of wally_params), 2, 3, 0, 0. */
+ *   mac_halves       0: the multiply-accumulate loads each plaintext tile
+ *                    whole into one buffer; 1: it works on half tiles,
+ *                    copying the next half into a second buffer while it
+ *                    multiplies the current one
+ * Defaults: 1024 (or the max_wave of wally_params), 2, 3, 0, 0, 0. */
 typedef struct {
     uint32_t max_wave;
     uint32_t lanes;
     uint32_t mac_ctas_per_sm;
     uint32_t ntt_ctas_per_sm;
     uint32_t ks_core;
+    uint32_t mac_halves;
 } wally_tuning;
 
 int wally_get_tuning(const wally_ctx *ctx, wally_tuning *out);
 
 /* Errors: WALLY_EINVAL (max_wave 0, lanes not 1 or 2, mac_ctas_per_sm not
- * 1..3, ks_core not 0 or 1).  An ntt_ctas_per_sm at or above what shared memory allows anyway is
+ * 1..3, ks_core or mac_halves not 0 or 1).  An ntt_ctas_per_sm at or above what shared memory allows anyway is
  * no cap.  Takes effect at the next call; it must not overlap running
  * evaluations of the context. */
 int wally_set_tuning(wally_ctx *ctx, const wally_tuning *tuning);
@@ -439,9 +444,10 @@ int wally_set_tuning(wally_ctx *ctx, const wally_tuning *tuning);
  * in the context and returns its index in *best.  With candidates non-NULL
  * the candidates are candidates[0 .. num_candidates).  With candidates NULL
  * (num_candidates 0) the search is staged: max_wave in {512, 1024, 2048} x
- * lanes in {1, 2} with mac 3, ntt 0, ks_core 0; then, at the best of those,
- * mac_ctas_per_sm in {2, 3} x ntt_ctas_per_sm in {0, 2}; then the best of
- * all with ks_core 1 (10 shapes in all).
+ * lanes in {1, 2} with mac 3, ntt 0, ks_core 0, mac_halves 0; then, at the
+ * best of those, mac_ctas_per_sm in {2, 3} x ntt_ctas_per_sm in {0, 2}; then
+ * the best so far with ks_core 1, then the best so far with mac_halves 1 (11
+ * shapes in all).
  * tried (host, [WALLY_AUTOTUNE_MAX] or [num_candidates], may be NULL)
  * receives the shapes in the order timed, ms_per_query (same length, may be
  * NULL) their mean device milliseconds per query of the sample, or -1 where

@@ -695,12 +695,14 @@ int apply_tuning(wally_ctx *c, const wally_tuning *t)
     if (t->lanes != 1 && t->lanes != 2) return fail(WALLY_EINVAL, "lanes must be 1 or 2");
     if (t->mac_ctas_per_sm < 1 || t->mac_ctas_per_sm > 3) return fail(WALLY_EINVAL, "mac_ctas_per_sm must be 1..3");
     if (t->ks_core > 1) return fail(WALLY_EINVAL, "ks_core must be 0 or 1");
+    if (t->mac_halves > 1) return fail(WALLY_EINVAL, "mac_halves must be 0 or 1");
     c->max_wave = t->max_wave;
     c->lanes_pref = t->lanes;
     c->dp.mac_ctas_per_sm = t->mac_ctas_per_sm;
     c->ntt_cps = t->ntt_ctas_per_sm;
     c->dp.ntt_smem = ntt_smem_for(c, t->ntt_ctas_per_sm);
     c->dp.ks_core = t->ks_core;
+    c->dp.mac_halves = t->mac_halves;
     return WALLY_OK;
 }
 
@@ -711,6 +713,7 @@ void current_tuning(const wally_ctx *c, wally_tuning *t)
     t->mac_ctas_per_sm = c->dp.mac_ctas_per_sm ? c->dp.mac_ctas_per_sm : 3;
     t->ntt_ctas_per_sm = c->ntt_cps;
     t->ks_core = c->dp.ks_core;
+    t->mac_halves = c->dp.mac_halves;
 }
 
 void release_waves(wally_ctx *c)
@@ -1459,7 +1462,7 @@ int wally_autotune(wally_ctx *c, const wally_tuning *cand, uint32_t nc, uint32_t
     if (cand && !nc) return fail(WALLY_EINVAL, "no candidates");
     for (uint32_t i = 0; cand && i < nc; i++)
         if (!cand[i].max_wave || (cand[i].lanes != 1 && cand[i].lanes != 2) || cand[i].mac_ctas_per_sm < 1 ||
-            cand[i].mac_ctas_per_sm > 3 || cand[i].ks_core > 1)
+            cand[i].mac_ctas_per_sm > 3 || cand[i].ks_core > 1 || cand[i].mac_halves > 1)
             return fail(WALLY_EINVAL, "invalid candidate shape %u", i);
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1488,18 +1491,24 @@ int wally_autotune(wally_ctx *c, const wally_tuning *cand, uint32_t nc, uint32_t
         for (uint32_t i = 0; i < nc && rc == WALLY_OK; i++) run(cand[i]);
     } else {
         for (uint32_t w : {512u, 1024u, 2048u})
-            for (uint32_t l : {1u, 2u}) run(wally_tuning{w, l, 3, 0, 0});
+            for (uint32_t l : {1u, 2u}) run(wally_tuning{w, l, 3, 0, 0, 0});
         const int b1 = best_of();
         if (rc == WALLY_OK && b1 >= 0) {
             const wally_tuning base = done[b1];
             for (uint32_t m : {2u, 3u})
                 for (uint32_t k : {0u, 2u})
-                    if (!(m == 3 && k == 0)) run(wally_tuning{base.max_wave, base.lanes, m, k, 0});
+                    if (!(m == 3 && k == 0)) run(wally_tuning{base.max_wave, base.lanes, m, k, 0, 0});
         }
         const int b2 = best_of();
         if (rc == WALLY_OK && b2 >= 0) {
             wally_tuning t = done[b2];
             t.ks_core = 1;
+            run(t);
+        }
+        const int b3 = best_of();
+        if (rc == WALLY_OK && b3 >= 0) {
+            wally_tuning t = done[b3];
+            t.mac_halves = 1;
             run(t);
         }
     }

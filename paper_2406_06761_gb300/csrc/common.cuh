@@ -65,6 +65,9 @@ struct DevParams {
     // transform core of the key-switch kernels: 0 = shared-memory radix-16
     // passes (three CTAs an SM), 1 = register-blocked passes (two CTAs an SM)
     u32 ks_core;
+    // multiply-accumulate: 0 = whole tiles, one buffer; 1 = half tiles,
+    // double-buffered with asynchronous copies
+    u32 mac_halves;
 };
 
 __device__ __forceinline__ u64 csub(u64 x, u64 m) { return x >= m ? x - m : x; }
@@ -326,6 +329,26 @@ __device__ __forceinline__ int pair_elem(int u)
 }
 
 __device__ __forceinline__ ulonglong2 ldg2(const u64 *p) { return __ldg(reinterpret_cast<const ulonglong2 *>(p)); }
+
+// L2 policy for data read once and not again soon (the keys of a key
+// switch): evicted first, so that the data a kernel parks in global memory
+// and reads back (transformed digits, key products) stays in L2.
+__device__ __forceinline__ u64 l2_evict_first_policy()
+{
+    u64 pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// 16-byte read-only load under an L2 policy.
+__device__ __forceinline__ ulonglong2 ldg2_hint(const u64 *p, u64 pol)
+{
+    ulonglong2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+                 : "=l"(v.x), "=l"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
 __device__ __forceinline__ void st2(u64 *p, u64 a, u64 b) { *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(a, b); }
 

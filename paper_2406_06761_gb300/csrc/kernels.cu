@@ -171,7 +171,7 @@ __device__ __forceinline__ void permute_and_digit_smem(const Smem<LOGN> &S, cons
     if (c == 1) {
         __syncthreads();
         poly_load<LOGN, true>(S.poly, sc_cj);  // this CTA's own writes
-        ntt_inv<LOGN>(S.poly, S.twi, md);
+        ntt_inv_keep<LOGN>(S.poly, S.twi, md);
 #pragma unroll 4
         for (int u = 0; u < 16; u++) {
             const int e = pair_elem<LOGN>(u), sp = spos(e);
@@ -184,7 +184,9 @@ __device__ __forceinline__ void permute_and_digit_smem(const Smem<LOGN> &S, cons
 //   u_j = sum_i NTT_j(d_i) * key_{i,j}  for both key components,
 // as one lazy 128-bit sum per output and a single Montgomery reduction (the
 // key is stored times 2^64).  NTT_j(d_j) = sigma(c1)_j is already known; the
-// other digits are transformed here, all but the last one parked in dd.  For
+// other digits are transformed here (lazy values below 56 p_j; a sum of L
+// products with keys below p_j stays below p_j 2^64), all but the last one
+// parked in dd.  For
 // j = P the sums are brought back to coefficients (r = [u]_P) for ModDown.
 template <int LOGN>
 __global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
@@ -202,19 +204,20 @@ __global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
     const int j = L - (int)(blockIdx.x % (L + 1));
     load_mod(&md, dpp, j);
     const u64 *kx = a.key + (size_t)(a.key_map ? a.key_map[x] : x) * a.key_stride;
+    const u64 pol = l2_evict_first_policy();  // keys: read once a key switch
     u64 *dd = a.dd + ((size_t)x * (L + 1) + j) * L * N;
     const int last = (j == L - 1) ? L - 2 : L - 1;  // the last digit transformed here
     for (int i = 0; i < L; i++) {
         if (i == j) continue;
         __syncthreads();
         poly_load<LOGN>(S.poly, a.dg + ((size_t)x * L + i) * N);  // < q_i < 8 p_j
-        ntt_fwd<LOGN>(S.poly, S.twf, md);
+        ntt_fwd_grow<LOGN>(S.poly, S.twf, md);  // lazy, < 56 p_j
         if (i != last) {
             u64 *di = dd + (size_t)i * N;
 #pragma unroll 4
             for (int u = 0; u < 16; u++) {
                 const int e = pair_elem<LOGN>(u), sp = spos(e);
-                st2(di + e, S.poly[sp], S.poly[sp ^ 1]);  // lazy, < 8 p_j
+                st2(di + e, S.poly[sp], S.poly[sp ^ 1]);  // lazy
             }
         }
     }
@@ -239,8 +242,8 @@ __global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
                 da = t.x;
                 db = t.y;
             }
-            const ulonglong2 kb = ldg2(kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N + e);
-            const ulonglong2 ka = ldg2(kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N + e);
+            const ulonglong2 kb = ldg2_hint(kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N + e, pol);
+            const ulonglong2 ka = ldg2_hint(kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N + e, pol);
             mac128(h0a, l0a, da, kb.x);
             mac128(h0b, l0b, db, kb.y);
             mac128(h1a, l1a, da, ka.x);
@@ -254,7 +257,7 @@ __global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
             u64 *uc = c ? u1 : u0;
             __syncthreads();
             poly_load<LOGN, true>(S.poly, uc);
-            ntt_inv<LOGN>(S.poly, S.twi, md);
+            ntt_inv_keep<LOGN>(S.poly, S.twi, md);
 #pragma unroll 4
             for (int u = 0; u < 16; u++) {
                 const int e = pair_elem<LOGN>(u), sp = spos(e);
@@ -287,15 +290,16 @@ __global__ void OLD_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
     load_mod(&md, dpp, j);
     const u64 q = md.p, P = dpp->m[L].p, half = (P - 1) / 2;
     const u64 pinv = dpp->pinv[j], pinv_s = dpp->pinv_s[j];
+    const u64 q64 = q << 6;
     const u64 *r = a.u + (((size_t)x * 2 + c) * (L + 1) + L) * N;
 #pragma unroll 4
     for (int u = 0; u < 16; u++) {
         const int e = pair_elem<LOGN>(u), sp = spos(e);
         const ulonglong2 rv = ldg2(r + e);
-        S.poly[sp] = rv.x > half ? q - (P - rv.x) : rv.x;  // r_c mod q_j, < 4q
+        S.poly[sp] = rv.x > half ? q - (P - rv.x) : rv.x;  // r_c mod q_j, < 2q
         S.poly[sp ^ 1] = rv.y > half ? q - (P - rv.y) : rv.y;
     }
-    ntt_fwd<LOGN>(S.poly, S.twf, md);
+    ntt_fwd_grow<LOGN>(S.poly, S.twf, md);  // < 58q
     const u64 *uj = a.u + (((size_t)x * 2 + c) * (L + 1) + j) * N;
     u64 *sc_cj = a.sc + ((size_t)x * 2 * L + c * L + j) * N;
     const u64 *ad = a.add ? a.add + x * a.add_stride + ((size_t)c * L + j) * N : nullptr;
@@ -304,8 +308,8 @@ __global__ void OLD_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
     for (int u = 0; u < 16; u++) {
         const int e = pair_elem<LOGN>(u), sp = spos(e);
         const ulonglong2 uv = ldg2(uj + e);
-        u64 v0 = csub(shoup_mul(uv.x + q - fwd_finish(S.poly[sp], md), pinv, pinv_s, q), q);
-        u64 v1 = csub(shoup_mul(uv.y + q - fwd_finish(S.poly[sp ^ 1], md), pinv, pinv_s, q), q);
+        u64 v0 = csub(shoup_mul(uv.x + q64 - S.poly[sp], pinv, pinv_s, q), q);
+        u64 v1 = csub(shoup_mul(uv.y + q64 - S.poly[sp ^ 1], pinv, pinv_s, q), q);
         if (c == 0) {
             const ulonglong2 s0 = ld2(sc_cj + e);
             v0 = addmod(v0, s0.x, q);
@@ -352,6 +356,7 @@ __global__ void NTT_LB(LOGN) k_ks_b_reg(const DevParams *dpp, RotArgs a)
     }
     const Mod &md = ms.md;
     const u64 *kx = a.key + (size_t)(a.key_map ? a.key_map[x] : x) * a.key_stride;
+    const u64 pol = l2_evict_first_policy();  // keys: read once a key switch
     const u64 *dd = a.dd + ((size_t)x * (L + 1) + j) * L * N;
     u64 *u0 = a.u + ((size_t)x * 2 + 0) * (L + 1) * N + (size_t)j * N;
     u64 *u1 = a.u + ((size_t)x * 2 + 1) * (L + 1) * N + (size_t)j * N;
@@ -375,8 +380,8 @@ __global__ void NTT_LB(LOGN) k_ks_b_reg(const DevParams *dpp, RotArgs a)
                 da = q.x;
                 db = q.y;
             }
-            const ulonglong2 kb = ldg2(kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N + e);
-            const ulonglong2 ka = ldg2(kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N + e);
+            const ulonglong2 kb = ldg2_hint(kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N + e, pol);
+            const ulonglong2 ka = ldg2_hint(kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N + e, pol);
             mac128(h0a, l0a, da, kb.x);
             mac128(h0b, l0b, db, kb.y);
             mac128(h1a, l1a, da, ka.x);
@@ -533,6 +538,116 @@ __global__ void __launch_bounds__(256, 2) k_mac(const DevParams *dpp, ClusterSto
             }
         }
     }
+}
+
+// The same products with the tile's two halves (ts/2 slot positions each)
+// as the unit of work, double-buffered: while a half is multiplied, the
+// next unit's half is copied into the other buffer with cp.async, so that
+// short segments (one query a cluster, as in the serving loop's waves) no
+// longer wait for their tile.  Two buffers of d_pad x ts/2 words take the
+// same shared memory as one whole tile.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+template <int G>
+__global__ void __launch_bounds__(256, 2) k_mac_halves(const DevParams *dpp, ClusterStore cs, WavePlan wp,
+                                                    const u64 *ctp, u64 *Tout, u32 m_max)
+{
+    extern __shared__ __align__(16) u64 sm[];
+    const int L = dpp->L, log_n = dpp->log_n, N = 1 << log_n;
+    const int h = dpp->h, dp_ = dpp->d_pad;
+    const int ts = cs.ts, hts = ts / 2, tiles = N / ts;
+    const size_t ctw = (size_t)2 * L * N;
+    const u32 nseg = wp.counts[2];
+    const u64 total = (u64)nseg * m_max * L * tiles * 2;  // units: (item, half)
+    const int slot_in = threadIdx.x % hts;
+    const int ql = threadIdx.x / hts;
+    const int QL = 256 / hts;
+    const size_t buf_words = (size_t)dp_ * hts;
+    // the unit's item, or false when its chunk does not exist (uniform)
+    auto decode = [&](u64 w, int &half, int &tile, int &l, int &k, u32 &seg, u32 &cl) {
+        half = (int)(w & 1);
+        u64 v = w >> 1;
+        tile = (int)(v % tiles);
+        u64 r = v / tiles;
+        l = (int)(r % L);
+        r /= L;
+        k = (int)(r % m_max);
+        seg = (u32)(r / m_max);
+        cl = wp.seg_cluster[seg];
+        return k < (int)cs.chunks[cl];
+    };
+    auto next_valid = [&](u64 w) {
+        int half, tile, l, k;
+        u32 seg, cl;
+        while (w < total && !decode(w, half, tile, l, k, seg, cl)) w += gridDim.x;
+        return w;
+    };
+    auto issue = [&](u64 w, u64 *buf) {
+        int half, tile, l, k;
+        u32 seg, cl;
+        decode(w, half, tile, l, k, seg, cl);
+        const u32 z = cs.chunk0[cl] + k;
+        const u64 *tsrc = cs.ptxt + (((size_t)z * L + l) * tiles + tile) * ((size_t)dp_ * ts) + half * hts;
+        const int per_row = hts / 2;  // 16-byte pieces a row
+        for (int q = threadIdx.x; q < dp_ * per_row; q += 256) {
+            const int row = q / per_row, col = (q % per_row) * 2;
+            cp_async16(buf + (size_t)row * hts + col, tsrc + (size_t)row * ts + col);
+        }
+    };
+    u64 w = next_valid(blockIdx.x);
+    int b = 0;
+    if (w < total) issue(w, sm);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    while (w < total) {
+        const u64 wn = next_valid(w + gridDim.x);
+        if (wn < total) issue(wn, sm + (b ^ 1) * buf_words);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        int half, tile, l, k;
+        u32 seg, cl;
+        decode(w, half, tile, l, k, seg, cl);
+        const u64 p = dpp->m[l].p, mni = dpp->m[l].mont_neg_inv;
+        const u64 *buf = sm + b * buf_words;
+        const int s = tile * ts + half * hts + slot_in;
+        const u32 sb = wp.seg_begin[seg], se = wp.seg_end[seg];
+        int IG = 1;
+        while (IG * 2 <= QL && IG * 2 <= h && (u32)(QL / (IG * 2)) >= se - sb) IG *= 2;
+        const int QLp = QL / IG, qlane = ql % QLp, ig = ql / QLp;
+        for (u32 pos = sb + qlane; pos < se; pos += QLp) {
+            const u64 *cq = ctp + (size_t)pos * G * ctw + (size_t)l * N + s;
+            u64 cb[G][2];
+#pragma unroll
+            for (int bb = 0; bb < G; bb++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) cb[bb][c] = cq[(size_t)bb * ctw + (size_t)c * L * N];
+            const u32 pr = wp.pair_off[pos] + k;
+            u64 *to = Tout + (size_t)pr * h * ctw + (size_t)l * N + s;
+            for (int i = ig; i < h; i += IG) {
+                u64 hi0 = 0, lo0 = 0, hi1 = 0, lo1 = 0;
+                const u64 *prow = buf + (size_t)i * G * hts + slot_in;
+#pragma unroll
+                for (int bb = 0; bb < G; bb++) {
+                    const u64 pv = prow[bb * hts];
+                    mac128(hi0, lo0, pv, cb[bb][0]);
+                    mac128(hi1, lo1, pv, cb[bb][1]);
+                }
+                Mod md;
+                md.p = p;
+                md.mont_neg_inv = mni;
+                to[(size_t)i * ctw] = mont_redc(hi0, lo0, md);
+                to[(size_t)i * ctw + (size_t)L * N] = mont_redc(hi1, lo1, md);
+            }
+        }
+        __syncthreads();  // the buffer is read out before the next prefetch refills it
+        w = wn;
+        b ^= 1;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // The same products for the other splits, mainly those with more than 32 baby
@@ -775,6 +890,9 @@ cudaError_t set_kernel_attributes(int log_n, u32 g)
     if (e != cudaSuccess) return e;
     (void)g;
     e = set_smem(k_mac<16, 2>, 64 * 1024);
+    if (e == cudaSuccess) e = set_smem(k_mac_halves<16>, 64 * 1024);
+    if (e == cudaSuccess) e = set_smem(k_mac_halves<8>, 64 * 1024);
+    if (e == cudaSuccess) e = set_smem(k_mac_halves<4>, 64 * 1024);
     if (e == cudaSuccess) e = set_smem(k_mac<8, 2>, 64 * 1024);
     if (e == cudaSuccess) e = set_smem(k_mac<4, 2>, 64 * 1024);
     if (e == cudaSuccess) e = set_smem(k_mac<32, 1>, 64 * 1024);
@@ -873,10 +991,20 @@ cudaError_t launch_mac(const DevParams &dp, const ClusterStore &cs, const WavePl
     if (grid > items) grid = items;
     if (grid == 0) return cudaSuccess;
     ProfScope ps(pr, KK_MAC, st);
+    const bool halves = dp.mac_halves && cs.ts % 4 == 0 && 256 % (cs.ts / 2) == 0;
     switch (dp.g) {
-    case 4: k_mac<4, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max); break;
-    case 8: k_mac<8, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max); break;
-    case 16: k_mac<16, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max); break;
+    case 4:
+        if (halves) k_mac_halves<4><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max);
+        else k_mac<4, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max);
+        break;
+    case 8:
+        if (halves) k_mac_halves<8><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max);
+        else k_mac<8, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max);
+        break;
+    case 16:
+        if (halves) k_mac_halves<16><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max);
+        else k_mac<16, 2><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max);
+        break;
     case 32: k_mac<32, 1><<<(unsigned)grid, 256, smem, st>>>(dpp, cs, wp, ctp, T, m_max); break;
     default:
         if (128 % cs.ts) return cudaErrorInvalidValue;

@@ -338,6 +338,128 @@ __device__ __forceinline__ void load_tw_cache_v(Tw *dst, const Tw *src)
     for (int i = threadIdx.x; i < C; i += P::T) d[i] = __ldg(s + i);
 }
 
+// ---------------------------------------------------------------------------
+// The shared-memory transform core (common.cuh: the polynomial in a swizzled
+// shared buffer, a remainder pass then radix-16 passes, each thread taking
+// its groups of 2^R elements from the buffer) with this file's butterflies:
+// the forward one without conditional subtractions (values grow by 4p a
+// stage) and both with the Shoup product in 32-bit multiply-adds.  The
+// twiddles of the passes served by the shared cache are read where they are
+// used rather than preloaded into registers, which frees registers for the
+// compiler to interleave a thread's two groups; the last pass (global table)
+// still loads its group's 15 twiddles first.
+
+template <int R, int ST, bool FWD, bool PRE>
+__device__ __forceinline__ void sgroup_stage(u64 *v, const Tw *tw, const Tw *tws, int S0, int hi, u64 np, u64 fp)
+{
+    constexpr int HD = 1 << (R - 1 - ST);
+    constexpr int NB = 1 << ST;
+#pragma unroll
+    for (int blk = 0; blk < NB; blk++) {
+        const Tw t = PRE ? tw[(NB - 1) + blk] : tws[(1 << (S0 + ST)) + ((hi << ST) | blk)];
+#pragma unroll
+        for (int j = 0; j < HD; j++) {
+            if constexpr (FWD) ct_grow(v[blk * 2 * HD + j], v[blk * 2 * HD + j + HD], t.w, t.ws, np, fp);
+            else gs_keep(v[blk * 2 * HD + j], v[blk * 2 * HD + j + HD], t.w, t.ws, np, fp);
+        }
+    }
+}
+
+template <int R, int ST, bool FWD, bool PRE>
+__device__ __forceinline__ void sgroup_stages(u64 *v, const Tw *tw, const Tw *tws, int S0, int hi, u64 np, u64 fp)
+{
+    if constexpr (FWD) {
+        if constexpr (ST < R) {
+            sgroup_stage<R, ST, true, PRE>(v, tw, tws, S0, hi, np, fp);
+            sgroup_stages<R, ST + 1, true, PRE>(v, tw, tws, S0, hi, np, fp);
+        }
+    } else {
+        if constexpr (ST >= 0) {
+            sgroup_stage<R, ST, false, PRE>(v, tw, tws, S0, hi, np, fp);
+            sgroup_stages<R, ST - 1, false, PRE>(v, tw, tws, S0, hi, np, fp);
+        }
+    }
+}
+
+// One pass of the shared-memory core (the group and twiddle indexing of
+// common.cuh's ntt_pass); PRE: preload the group's twiddles (global table).
+template <int LOGN, int R, bool FWD, bool PRE>
+__device__ __forceinline__ void spass(u64 *sm, int S0, const Tw *tws, u64 np, u64 fp)
+{
+    constexpr int T = NttShape<LOGN>::T;
+    constexpr int G = 1 << R;
+    constexpr int NG = 32 / G;
+    const int BLO = LOGN - R - S0;
+    const int tid = threadIdx.x;
+#pragma unroll 2
+    for (int u = 0; u < NG; u++) {
+        const int gi = tid + T * u;
+        const int lo = gi & ((1 << BLO) - 1);
+        const int hi = gi >> BLO;
+        const int base = (hi << (BLO + R)) | lo;
+        Tw tw[PRE ? G - 1 : 1];
+        if constexpr (PRE) {
+#pragma unroll
+            for (int st = 0, k = 0; st < R; st++)
+#pragma unroll
+                for (int blk = 0; blk < (1 << st); blk++, k++) tw[k] = tws[(1 << (S0 + st)) + ((hi << st) | blk)];
+        }
+        u64 v[G];
+#pragma unroll
+        for (int k = 0; k < G; k++) v[k] = sm[spos(base + (k << BLO))];
+        if constexpr (FWD) sgroup_stages<R, 0, true, PRE>(v, tw, tws, S0, hi, np, fp);
+        else sgroup_stages<R, R - 1, false, PRE>(v, tw, tws, S0, hi, np, fp);
+#pragma unroll
+        for (int k = 0; k < G; k++) sm[spos(base + (k << BLO))] = v[k];
+    }
+}
+
+// Forward transform of the shared-memory core with growing values: inputs
+// below B, outputs below B + 4p log2 N (the order and positions of
+// common.cuh's ntt_fwd).  Starts and ends with __syncthreads().
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd_grow(u64 *sm, Tw *cache, const Mod &md)
+{
+    using S = NttShape<LOGN>;
+    const u64 np = md.np, fp = md.four_p;
+    __syncthreads();
+    load_tw_cache<LOGN>(cache, md.fwd);
+    __syncthreads();
+    if constexpr (S::RR > 0) {
+        spass<LOGN, S::RR, true, false>(sm, 0, cache, np, fp);
+        __syncthreads();
+    }
+#pragma unroll 1
+    for (int s0 = S::RR; s0 < LOGN - 4; s0 += 4) {
+        spass<LOGN, 4, true, false>(sm, s0, cache, np, fp);
+        __syncthreads();
+    }
+    spass<LOGN, 4, true, true>(sm, LOGN - 4, md.fwd, np, fp);
+    __syncthreads();
+}
+
+// Inverse transform of the shared-memory core (values < 4p in and out, as
+// common.cuh's ntt_inv).  Starts and ends with __syncthreads().
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv_keep(u64 *sm, Tw *cache, const Mod &md)
+{
+    using S = NttShape<LOGN>;
+    const u64 np = md.np, fp = md.four_p;
+    __syncthreads();
+    load_tw_cache<LOGN>(cache, md.inv);
+    spass<LOGN, 4, false, true>(sm, LOGN - 4, md.inv, np, fp);
+    __syncthreads();
+#pragma unroll 1
+    for (int s0 = LOGN - 8; s0 >= S::RR; s0 -= 4) {
+        spass<LOGN, 4, false, false>(sm, s0, cache, np, fp);
+        __syncthreads();
+    }
+    if constexpr (S::RR > 0) {
+        spass<LOGN, S::RR, false, false>(sm, 0, cache, np, fp);
+        __syncthreads();
+    }
+}
+
 // x < 64p -> [0, p)
 __device__ __forceinline__ u64 reduce64p(u64 x, const Mod &md)
 {

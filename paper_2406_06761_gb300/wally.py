@@ -51,7 +51,7 @@ class wally_info(ctypes.Structure):
 
 class wally_tuning(ctypes.Structure):
     _fields_ = [("max_wave", ctypes.c_uint32), ("lanes", ctypes.c_uint32), ("mac_ctas_per_sm", ctypes.c_uint32),
-                ("ntt_ctas_per_sm", ctypes.c_uint32), ("ks_core", ctypes.c_uint32)]
+                ("ntt_ctas_per_sm", ctypes.c_uint32), ("ks_core", ctypes.c_uint32), ("mac_halves", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -380,8 +380,8 @@ def wally_get_tuning(ctx: int) -> wally_tuning:
 
 
 def wally_set_tuning(ctx: int, max_wave: int, lanes: int = 2, mac_ctas_per_sm: int = 3,
-                     ntt_ctas_per_sm: int = 0, ks_core: int = 0) -> None:
-    t = wally_tuning(max_wave, lanes, mac_ctas_per_sm, ntt_ctas_per_sm, ks_core)
+                     ntt_ctas_per_sm: int = 0, ks_core: int = 0, mac_halves: int = 0) -> None:
+    t = wally_tuning(max_wave, lanes, mac_ctas_per_sm, ntt_ctas_per_sm, ks_core, mac_halves)
     _check(load().wally_set_tuning(ctx, ctypes.byref(t)))
 
 

@@ -45,8 +45,8 @@ def test_recorded_traffic_is_scaled_per_item_and_gated_by_the_source_hash():
     t = b.recorded_traffic("ks_b")
     if t is None:  # the committed capture predates the current kernel sources
         return
-    assert b.recorded_traffic("ks_b", 1024) == t
-    assert abs(b.recorded_traffic("ks_b", 2048) - 2 * t) < 1
+    t1 = b.recorded_traffic("ks_b", 1)
+    assert abs(b.recorded_traffic("ks_b", 2048) - 2048 * t1) < 1e-3 * 2048 * t1
     assert b.recorded_traffic("no_such_kernel") is None
 
 

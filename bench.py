@@ -137,7 +137,7 @@ def recorded_traffic(kernel: str, items_per_launch: float | None = None):
 def work_per_kind(L: int, N: int, log_n: int, queries: int, pairs: int, g: int, h: int) -> dict:
     """Modular operations the method performs in each kernel kind, split by
     class -- NTT butterflies (bfly), Shoup products by a constant (mm) and
-    64x64 -> 128-bit multiply-accumulates (mac) -- for `queries` queries with
+    exact multiply-accumulates into 128-bit sums (mac) -- for `queries` queries with
     `pairs` (query, chunk) products in all.  A transform of N points is
     N/2 log2 N butterflies; an inverse adds N scalings by N^-1.  Key switch
     (ks_b): L^2 forward transforms of the digits into the other moduli, the
@@ -586,7 +586,7 @@ def main():
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of a small case "
                                   "(profiles/), scaled to this run's mean items per launch",
                 "peak_source": "measured: wally_measure_int_peaks (the transforms' forward butterfly in registers, "
-                               "all SMs, this GPU); Shoup products and 128-bit multiply-accumulates counted as "
+                               "all SMs, this GPU); Shoup products and exact multiply-accumulates counted as "
                                "butterflies by the ratio of their own measured peaks",
                 "issue_source": "measured: wally_measure_pipe_rates (2 mul.hi + 3 mad.wide + 4 mad.lo a butterfly "
                                 "on the integer multiplier)",

@@ -373,8 +373,9 @@ int wally_profile_waves(wally_ctx *ctx, uint32_t cap, uint32_t *call, uint32_t *
  * independent operations, no memory traffic): 64-bit Shoup modular
  * multiplications, NTT butterflies (the forward butterfly the transforms
  * use: one Shoup product written out in 32-bit multiply-adds plus three
- * 64-bit additions), and 64x64 -> 128-bit multiply-accumulates, each in
- * operations per second.  Used as the denominator of the integer-ALU
+ * 64-bit additions), and exact multiply-accumulates of operands below 2^56
+ * into a 128-bit sum (in the kernels' form: four 32-bit multiply-adds on
+ * 28-bit limbs), each in operations per second.  Used as the denominator of the integer-ALU
  * roofline.  Synchronous; allocates a few kilobytes. */
 int wally_measure_int_peaks(int32_t device, double *modmul_per_s, double *butterfly_per_s, double *mac128_per_s);
 

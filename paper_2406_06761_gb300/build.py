@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libwally.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["kernels.cu", "kernels_client.cu", "api.cu", "host_nt.cpp", "peaks.cu", "noalloc.cu", "pir.cu", "plan.cpp"]
-HEADERS = ["common.cuh", "kernels.hpp", "host_nt.hpp", "ctx_access.hpp", "pir.hpp", "plan.hpp"]
+HEADERS = ["common.cuh", "ntt_regs.cuh", "kernels.hpp", "host_nt.hpp", "ctx_access.hpp", "pir.hpp", "plan.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr",
          "-I", INCLUDE]

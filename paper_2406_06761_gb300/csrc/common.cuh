@@ -108,6 +108,60 @@ __device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b)
         : "l"(a), "l"(b));
 }
 
+// Sums of up to 32 products of operands below 2^56, exactly: each operand split into 28-bit limbs a = a1 2^28 + a0,
+// the four 32x32 -> 64-bit limb products accumulated in three columns of
+// weight 1, 2^28 and 2^56 (each column stays below 2^63), combined into the
+// 128-bit sum once at the end.  Four 32-bit multiply-adds a product instead
+// of a 64x64 -> 128-bit multiply-accumulate.
+struct Acc28 {
+    u64 c0, c1, c2;
+};
+
+__device__ __forceinline__ void split28(u64 x, u32 &x0, u32 &x1)
+{
+    x0 = (u32)x & 0x0FFFFFFFu;
+    x1 = (u32)(x >> 28);
+}
+
+// c0 + c1 2^28 + c2 2^56 as (hi, lo).
+__device__ __forceinline__ void acc28_sum(const Acc28 &a, u64 &hi, u64 &lo)
+{
+    const u64 t1 = a.c1 << 28, t1h = a.c1 >> 36, t2 = a.c2 << 56, t2h = a.c2 >> 8;
+    asm("add.cc.u64 %0, %2, %3;\n\t"
+        "addc.u64 %1, %4, 0;\n\t"
+        "add.cc.u64 %0, %0, %5;\n\t"
+        "addc.u64 %1, %1, %6;"
+        : "=l"(lo), "=l"(hi)
+        : "l"(a.c0), "l"(t1), "l"(t1h), "l"(t2), "l"(t2h));
+}
+
+__device__ __forceinline__ void acc28_zero(Acc28 &a) { a.c0 = a.c1 = a.c2 = 0; }
+
+__device__ __forceinline__ void mac28(Acc28 &acc, u32 a0, u32 a1, u32 b0, u32 b1)
+{
+    acc.c0 += (u64)a0 * b0;
+    acc.c1 += (u64)a0 * b1;
+    acc.c1 += (u64)a1 * b0;
+    acc.c2 += (u64)a1 * b1;
+}
+
+// acc += a * b with a given in limbs and b whole.
+__device__ __forceinline__ void mac28(Acc28 &acc, u32 a0, u32 a1, u64 b)
+{
+    u32 b0, b1;
+    split28(b, b0, b1);
+    mac28(acc, a0, a1, b0, b1);
+}
+
+// The accumulated sum times 2^-64 mod p (Montgomery reduction); the sum's
+// high word must be below p.
+__device__ __forceinline__ u64 acc28_redc(const Acc28 &a, const Mod &md)
+{
+    u64 hi, lo;
+    acc28_sum(a, hi, lo);
+    return mont_redc(hi, lo, md);
+}
+
 __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 p) { return csub(a + b, p); }
 __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + p - b; }
 

@@ -169,14 +169,10 @@ __device__ __forceinline__ void permute_and_digit_smem(const Smem<LOGN> &S, cons
         st2(sc_cj + e, S.poly[spos(galois_src(e, k, LOGN))], S.poly[spos(galois_src(e + 1, k, LOGN))]);
     }
     if (c == 1) {
-        __syncthreads();
-        poly_load<LOGN, true>(S.poly, sc_cj);  // this CTA's own writes
-        ntt_inv_keep<LOGN>(S.poly, S.twi, md);
-#pragma unroll 4
-        for (int u = 0; u < 16; u++) {
-            const int e = pair_elem<LOGN>(u), sp = spos(e);
-            st2(dg_j + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp ^ 1], md));
-        }
+        // the inverse reads its first pass from sc_cj (this CTA's own writes,
+        // visible after the barrier it starts with) and stores the digit
+        ntt_inv_keep_from<LOGN, true>(S.poly, S.twi, sc_cj, md);
+        inv_store_last<LOGN>(S.poly, dg_j, md);
     }
 }
 
@@ -209,9 +205,9 @@ __global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
     const int last = (j == L - 1) ? L - 2 : L - 1;  // the last digit transformed here
     for (int i = 0; i < L; i++) {
         if (i == j) continue;
-        __syncthreads();
-        poly_load<LOGN>(S.poly, a.dg + ((size_t)x * L + i) * N);  // < q_i < 8 p_j
-        ntt_fwd_grow<LOGN>(S.poly, S.twf, md);  // lazy, < 56 p_j
+        // digit i (< q_i < 2 p_j), its first stage fused into the load
+        fwd_load_first<LOGN, false>(S.poly, S.twf, a.dg + ((size_t)x * L + i) * N, [](u64 v, int) { return v; }, md);
+        ntt_fwd_grow_rest<LOGN>(S.poly, S.twf, md);  // lazy, < 56 p_j
         if (i != last) {
             u64 *di = dd + (size_t)i * N;
 #pragma unroll 4
@@ -227,7 +223,8 @@ __global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
 #pragma unroll 2
     for (int u = 0; u < 16; u++) {
         const int e = pair_elem<LOGN>(u), sp = spos(e);
-        u64 h0a = 0, l0a = 0, h0b = 0, l0b = 0, h1a = 0, l1a = 0, h1b = 0, l1b = 0;
+        Acc28 s0a, s0b, s1a, s1b;  // digits < 56 p_j, keys < p_j, L <= 32 terms
+        acc28_zero(s0a), acc28_zero(s0b), acc28_zero(s1a), acc28_zero(s1b);
         for (int i = 0; i < L; i++) {
             u64 da, db;
             if (i == j) {
@@ -244,25 +241,22 @@ __global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
             }
             const ulonglong2 kb = ldg2_hint(kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N + e, pol);
             const ulonglong2 ka = ldg2_hint(kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N + e, pol);
-            mac128(h0a, l0a, da, kb.x);
-            mac128(h0b, l0b, db, kb.y);
-            mac128(h1a, l1a, da, ka.x);
-            mac128(h1b, l1b, db, ka.y);
+            u32 a0, a1, b0, b1;
+            split28(da, a0, a1);
+            split28(db, b0, b1);
+            mac28(s0a, a0, a1, kb.x);
+            mac28(s0b, b0, b1, kb.y);
+            mac28(s1a, a0, a1, ka.x);
+            mac28(s1b, b0, b1, ka.y);
         }
-        st2(u0 + e, mont_redc(h0a, l0a, md), mont_redc(h0b, l0b, md));
-        st2(u1 + e, mont_redc(h1a, l1a, md), mont_redc(h1b, l1b, md));
+        st2(u0 + e, acc28_redc(s0a, md), acc28_redc(s0b, md));
+        st2(u1 + e, acc28_redc(s1a, md), acc28_redc(s1b, md));
     }
     if (j == L) {
         for (int c = 0; c < 2; c++) {
             u64 *uc = c ? u1 : u0;
-            __syncthreads();
-            poly_load<LOGN, true>(S.poly, uc);
-            ntt_inv_keep<LOGN>(S.poly, S.twi, md);
-#pragma unroll 4
-            for (int u = 0; u < 16; u++) {
-                const int e = pair_elem<LOGN>(u), sp = spos(e);
-                st2(uc + e, inv_finish(S.poly[sp], md), inv_finish(S.poly[sp ^ 1], md));
-            }
+            ntt_inv_keep_from<LOGN, true>(S.poly, S.twi, uc, md);  // this CTA's own writes
+            inv_store_last<LOGN>(S.poly, uc, md);
         }
     }
 }
@@ -292,14 +286,9 @@ __global__ void OLD_LB(LOGN) k_ks_c(const DevParams *dpp, RotArgs a)
     const u64 pinv = dpp->pinv[j], pinv_s = dpp->pinv_s[j];
     const u64 q64 = q << 6;
     const u64 *r = a.u + (((size_t)x * 2 + c) * (L + 1) + L) * N;
-#pragma unroll 4
-    for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = spos(e);
-        const ulonglong2 rv = ldg2(r + e);
-        S.poly[sp] = rv.x > half ? q - (P - rv.x) : rv.x;  // r_c mod q_j, < 2q
-        S.poly[sp ^ 1] = rv.y > half ? q - (P - rv.y) : rv.y;
-    }
-    ntt_fwd_grow<LOGN>(S.poly, S.twf, md);  // < 58q
+    // r_c mod q_j (< 2q), the first forward stage fused into the load
+    fwd_load_first<LOGN, false>(S.poly, S.twf, r, [=](u64 v, int) { return v > half ? q - (P - v) : v; }, md);
+    ntt_fwd_grow_rest<LOGN>(S.poly, S.twf, md);  // < 58q
     const u64 *uj = a.u + (((size_t)x * 2 + c) * (L + 1) + j) * N;
     u64 *sc_cj = a.sc + ((size_t)x * 2 * L + c * L + j) * N;
     const u64 *ad = a.add ? a.add + x * a.add_stride + ((size_t)c * L + j) * N : nullptr;
@@ -365,7 +354,8 @@ __global__ void NTT_LB(LOGN) k_ks_b_reg(const DevParams *dpp, RotArgs a)
 #pragma unroll
     for (int k = 0; k < 32; k += 2) {
         const int e = elem_last<P>(t, k);
-        u64 h0a = 0, l0a = 0, h0b = 0, l0b = 0, h1a = 0, l1a = 0, h1b = 0, l1b = 0;
+        Acc28 s0a, s0b, s1a, s1b;  // digits < 56 p_j, keys < p_j, L <= 32 terms
+        acc28_zero(s0a), acc28_zero(s0b), acc28_zero(s1a), acc28_zero(s1b);
         for (int i = 0; i < L; i++) {
             u64 da, db;
             if (i == j) {
@@ -382,13 +372,16 @@ __global__ void NTT_LB(LOGN) k_ks_b_reg(const DevParams *dpp, RotArgs a)
             }
             const ulonglong2 kb = ldg2_hint(kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N + e, pol);
             const ulonglong2 ka = ldg2_hint(kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N + e, pol);
-            mac128(h0a, l0a, da, kb.x);
-            mac128(h0b, l0b, db, kb.y);
-            mac128(h1a, l1a, da, ka.x);
-            mac128(h1b, l1b, db, ka.y);
+            u32 a0, a1, b0, b1;
+            split28(da, a0, a1);
+            split28(db, b0, b1);
+            mac28(s0a, a0, a1, kb.x);
+            mac28(s0b, b0, b1, kb.y);
+            mac28(s1a, a0, a1, ka.x);
+            mac28(s1b, b0, b1, ka.y);
         }
-        st2(u0 + e, mont_redc(h0a, l0a, md), mont_redc(h0b, l0b, md));
-        st2(u1 + e, mont_redc(h1a, l1a, md), mont_redc(h1b, l1b, md));
+        st2(u0 + e, acc28_redc(s0a, md), acc28_redc(s0b, md));
+        st2(u1 + e, acc28_redc(s1a, md), acc28_redc(s1b, md));
     }
     if (j == L) {
         for (int c = 0; c < 2; c++) {
@@ -470,7 +463,8 @@ __global__ void NTT_LB(LOGN) k_ks_c_reg(const DevParams *dpp, RotArgs a)
 // slot positions): load the tile of P'_{k,i,b} (d_pad x ts words) into shared
 // memory once, then for every query of the segment
 //   T_i[c] = sum_b P'_{k,i,b} * ct'[b][c]  (i < h, c = 0, 1)
-// with 128-bit lazy accumulation and one Montgomery reduction per output
+// with exact lazy accumulation (28-bit limb columns) and one Montgomery
+// reduction per output
 // (plaintexts are stored times 2^64, Sec. 7 lazy reduction).
 template <int G, int CPT>
 __global__ void __launch_bounds__(256, 2) k_mac(const DevParams *dpp, ClusterStore cs, WavePlan wp, const u64 *ctp,
@@ -515,26 +509,27 @@ __global__ void __launch_bounds__(256, 2) k_mac(const DevParams *dpp, ClusterSto
         const int QLp = QL / IG, qlane = ql % QLp, ig = ql / QLp;
         for (u32 pos = sb + qlane; pos < se; pos += QLp) {
             const u64 *cq = ctp + (size_t)pos * G * ctw + (size_t)l * N + s;
-            u64 cb[G][CPT];
+            u32 cb0[G][CPT], cb1[G][CPT];  // in 28-bit limbs
 #pragma unroll
             for (int b = 0; b < G; b++)
 #pragma unroll
-                for (int c = 0; c < CPT; c++) cb[b][c] = cq[(size_t)b * ctw + (size_t)(c + comp) * L * N];
+                for (int c = 0; c < CPT; c++) split28(cq[(size_t)b * ctw + (size_t)(c + comp) * L * N], cb0[b][c], cb1[b][c]);
             const u32 p = wp.pair_off[pos] + k;
             u64 *to = Tout + (size_t)p * h * ctw + (size_t)l * N + s;
             for (int i = ig; i < h; i += IG) {
-                u64 hi[CPT], lo[CPT];
+                Acc28 acc[CPT];  // operands < p, G <= 32 terms
 #pragma unroll
-                for (int c = 0; c < CPT; c++) hi[c] = lo[c] = 0;
+                for (int c = 0; c < CPT; c++) acc28_zero(acc[c]);
                 const u64 *prow = sm + (size_t)i * G * ts + slot_in;
 #pragma unroll
                 for (int b = 0; b < G; b++) {
-                    const u64 pv = prow[b * ts];
+                    u32 p0, p1;
+                    split28(prow[b * ts], p0, p1);
 #pragma unroll
-                    for (int c = 0; c < CPT; c++) mac128(hi[c], lo[c], pv, cb[b][c]);
+                    for (int c = 0; c < CPT; c++) mac28(acc[c], p0, p1, cb0[b][c], cb1[b][c]);
                 }
 #pragma unroll
-                for (int c = 0; c < CPT; c++) to[(size_t)i * ctw + (size_t)(c + comp) * L * N] = mont_redc(hi[c], lo[c], md);
+                for (int c = 0; c < CPT; c++) to[(size_t)i * ctw + (size_t)(c + comp) * L * N] = acc28_redc(acc[c], md);
             }
         }
     }
@@ -620,27 +615,29 @@ __global__ void __launch_bounds__(256, 2) k_mac_halves(const DevParams *dpp, Clu
         const int QLp = QL / IG, qlane = ql % QLp, ig = ql / QLp;
         for (u32 pos = sb + qlane; pos < se; pos += QLp) {
             const u64 *cq = ctp + (size_t)pos * G * ctw + (size_t)l * N + s;
-            u64 cb[G][2];
+            u32 cb0[G][2], cb1[G][2];  // in 28-bit limbs
 #pragma unroll
             for (int bb = 0; bb < G; bb++)
 #pragma unroll
-                for (int c = 0; c < 2; c++) cb[bb][c] = cq[(size_t)bb * ctw + (size_t)c * L * N];
+                for (int c = 0; c < 2; c++) split28(cq[(size_t)bb * ctw + (size_t)c * L * N], cb0[bb][c], cb1[bb][c]);
             const u32 pr = wp.pair_off[pos] + k;
             u64 *to = Tout + (size_t)pr * h * ctw + (size_t)l * N + s;
             for (int i = ig; i < h; i += IG) {
-                u64 hi0 = 0, lo0 = 0, hi1 = 0, lo1 = 0;
+                Acc28 s0, s1;  // operands < p, G <= 16 terms
+                acc28_zero(s0), acc28_zero(s1);
                 const u64 *prow = buf + (size_t)i * G * hts + slot_in;
 #pragma unroll
                 for (int bb = 0; bb < G; bb++) {
-                    const u64 pv = prow[bb * hts];
-                    mac128(hi0, lo0, pv, cb[bb][0]);
-                    mac128(hi1, lo1, pv, cb[bb][1]);
+                    u32 p0, p1;
+                    split28(prow[bb * hts], p0, p1);
+                    mac28(s0, p0, p1, cb0[bb][0], cb1[bb][0]);
+                    mac28(s1, p0, p1, cb0[bb][1], cb1[bb][1]);
                 }
                 Mod md;
                 md.p = p;
                 md.mont_neg_inv = mni;
-                to[(size_t)i * ctw] = mont_redc(hi0, lo0, md);
-                to[(size_t)i * ctw + (size_t)L * N] = mont_redc(hi1, lo1, md);
+                to[(size_t)i * ctw] = acc28_redc(s0, md);
+                to[(size_t)i * ctw + (size_t)L * N] = acc28_redc(s1, md);
             }
         }
         __syncthreads();  // the buffer is read out before the next prefetch refills it

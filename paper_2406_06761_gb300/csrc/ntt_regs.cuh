@@ -460,6 +460,185 @@ __device__ __forceinline__ void ntt_inv_keep(u64 *sm, Tw *cache, const Mod &md)
     }
 }
 
+// The same transforms with their first (forward) or last (inverse) memory
+// pass fused into the global load or store: the RR = log2 N mod 4 stages of
+// the remainder pass pair elements N/2 (and N/4) apart, so a thread that
+// loads an element together with its partners can run them before the
+// polynomial first reaches shared memory; and the inverse's first pass works
+// on 16 contiguous elements, which it can read straight from global memory.
+
+// Load of the input with the forward remainder stages: element e of the
+// buffer gets f(src[e], e) transformed by stages 0 .. RR-1 (values grow by
+// 4p a stage).  Ends with a barrier, after which ntt_fwd_grow_rest runs the
+// remaining passes.  Loads the shared twiddle cache.
+template <int LOGN, bool COHERENT, class F>
+__device__ __forceinline__ void fwd_load_first(u64 *sm, Tw *cache, const u64 *src, F f, const Mod &md)
+{
+    using S = NttShape<LOGN>;
+    constexpr int N = 1 << LOGN, T = S::T;
+    const u64 np = md.np, fp = md.four_p;
+    const int t = threadIdx.x;
+    __syncthreads();  // earlier users of sm and the cache are done
+    load_tw_cache<LOGN>(cache, md.fwd);
+    auto ld = [&](int e) { return COHERENT ? ld2(src + e) : ldg2(src + e); };
+    if constexpr (S::RR == 0) {
+#pragma unroll 4
+        for (int u = 0; u < 16; u++) {
+            const int e = 2 * (t + T * u), sp = spos(e);
+            const ulonglong2 a = ld(e);
+            sm[sp] = f(a.x, e);
+            sm[sp ^ 1] = f(a.y, e + 1);
+        }
+    } else if constexpr (S::RR == 1) {
+        const Tw w1 = md.fwd[1];
+#pragma unroll 2
+        for (int u = 0; u < N / (4 * T); u++) {
+            const int e = 2 * (t + T * u), sp = spos(e), sq = spos(e + N / 2);
+            const ulonglong2 a = ld(e), b = ld(e + N / 2);
+            u64 x0 = f(a.x, e), x1 = f(a.y, e + 1), y0 = f(b.x, e + N / 2), y1 = f(b.y, e + 1 + N / 2);
+            ct_grow(x0, y0, w1.w, w1.ws, np, fp);
+            ct_grow(x1, y1, w1.w, w1.ws, np, fp);
+            sm[sp] = x0;
+            sm[sp ^ 1] = x1;
+            sm[sq] = y0;
+            sm[sq ^ 1] = y1;
+        }
+    } else {
+        const Tw w1 = md.fwd[1], w2 = md.fwd[2], w3 = md.fwd[3];
+#pragma unroll 1
+        for (int u = 0; u < N / (8 * T); u++) {
+            const int e0 = 2 * (t + T * u);
+            u64 v[2][4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const ulonglong2 a = ld(e0 + q * (N / 4));
+                v[0][q] = f(a.x, e0 + q * (N / 4));
+                v[1][q] = f(a.y, e0 + 1 + q * (N / 4));
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                ct_grow(v[h][0], v[h][2], w1.w, w1.ws, np, fp);  // stage 0: N/2 apart
+                ct_grow(v[h][1], v[h][3], w1.w, w1.ws, np, fp);
+                ct_grow(v[h][0], v[h][1], w2.w, w2.ws, np, fp);  // stage 1: N/4 apart, two blocks
+                ct_grow(v[h][2], v[h][3], w3.w, w3.ws, np, fp);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int sp = spos(e0 + q * (N / 4));
+                sm[sp] = v[0][q];
+                sm[sp ^ 1] = v[1][q];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// The forward passes after fwd_load_first.  Ends with a barrier.
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd_grow_rest(u64 *sm, const Tw *cache, const Mod &md)
+{
+    using S = NttShape<LOGN>;
+    const u64 np = md.np, fp = md.four_p;
+#pragma unroll 1
+    for (int s0 = S::RR; s0 < LOGN - 4; s0 += 4) {
+        spass<LOGN, 4, true, false>(sm, s0, cache, np, fp);
+        __syncthreads();
+    }
+    spass<LOGN, 4, true, true>(sm, LOGN - 4, md.fwd, np, fp);
+    __syncthreads();
+}
+
+// The inverse's first pass (the last radix-16 stages, groups of 16
+// contiguous elements) read from global memory (values < 4p), results into
+// the shared buffer; then the middle passes.  Loads the shared twiddle
+// cache; ends with a barrier, after which inv_store_last finishes.
+template <int LOGN, bool COHERENT>
+__device__ __forceinline__ void ntt_inv_keep_from(u64 *sm, Tw *cache, const u64 *src, const Mod &md)
+{
+    using S = NttShape<LOGN>;
+    constexpr int T = S::T, S0 = LOGN - 4;
+    const u64 np = md.np, fp = md.four_p;
+    const int tid = threadIdx.x;
+    __syncthreads();  // earlier users of sm and the cache are done
+    load_tw_cache<LOGN>(cache, md.inv);
+#pragma unroll 2
+    for (int u = 0; u < 2; u++) {
+        const int hi = tid + T * u, base = hi << 4;
+        Tw tw[15];
+#pragma unroll
+        for (int st = 0, k = 0; st < 4; st++)
+#pragma unroll
+            for (int blk = 0; blk < (1 << st); blk++, k++) tw[k] = md.inv[(1 << (S0 + st)) + ((hi << st) | blk)];
+        u64 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; k += 2) {
+            const ulonglong2 a = COHERENT ? ld2(src + base + k) : ldg2(src + base + k);
+            v[k] = a.x;
+            v[k + 1] = a.y;
+        }
+        sgroup_stages<4, 3, false, true>(v, tw, nullptr, S0, hi, np, fp);
+#pragma unroll
+        for (int k = 0; k < 16; k++) sm[spos(base + k)] = v[k];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int s0 = LOGN - 8; s0 >= S::RR; s0 -= 4) {
+        spass<LOGN, 4, false, false>(sm, s0, cache, np, fp);
+        __syncthreads();
+    }
+}
+
+// The inverse's remainder stages fused with the store: coefficient e (times
+// N, scaled back by N^-1) to dst[e], canonical.
+template <int LOGN>
+__device__ __forceinline__ void inv_store_last(const u64 *sm, u64 *dst, const Mod &md)
+{
+    using S = NttShape<LOGN>;
+    constexpr int N = 1 << LOGN, T = S::T;
+    const u64 np = md.np, fp = md.four_p;
+    const int t = threadIdx.x;
+    if constexpr (S::RR == 0) {
+#pragma unroll 4
+        for (int u = 0; u < 16; u++) {
+            const int e = 2 * (t + T * u), sp = spos(e);
+            st2(dst + e, inv_finish(sm[sp], md), inv_finish(sm[sp ^ 1], md));
+        }
+    } else if constexpr (S::RR == 1) {
+        const Tw w1 = md.inv[1];
+#pragma unroll 2
+        for (int u = 0; u < N / (4 * T); u++) {
+            const int e = 2 * (t + T * u), sp = spos(e), sq = spos(e + N / 2);
+            u64 x0 = sm[sp], x1 = sm[sp ^ 1], y0 = sm[sq], y1 = sm[sq ^ 1];
+            gs_keep(x0, y0, w1.w, w1.ws, np, fp);
+            gs_keep(x1, y1, w1.w, w1.ws, np, fp);
+            st2(dst + e, inv_finish(x0, md), inv_finish(x1, md));
+            st2(dst + e + N / 2, inv_finish(y0, md), inv_finish(y1, md));
+        }
+    } else {
+        const Tw w1 = md.inv[1], w2 = md.inv[2], w3 = md.inv[3];
+#pragma unroll 1
+        for (int u = 0; u < N / (8 * T); u++) {
+            const int e0 = 2 * (t + T * u);
+            u64 v[2][4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int sp = spos(e0 + q * (N / 4));
+                v[0][q] = sm[sp];
+                v[1][q] = sm[sp ^ 1];
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                gs_keep(v[h][0], v[h][1], w2.w, w2.ws, np, fp);  // stage 1 first
+                gs_keep(v[h][2], v[h][3], w3.w, w3.ws, np, fp);
+                gs_keep(v[h][0], v[h][2], w1.w, w1.ws, np, fp);  // then stage 0
+                gs_keep(v[h][1], v[h][3], w1.w, w1.ws, np, fp);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) st2(dst + e0 + q * (N / 4), inv_finish(v[0][q], md), inv_finish(v[1][q], md));
+        }
+    }
+}
+
 // x < 64p -> [0, p)
 __device__ __forceinline__ u64 reduce64p(u64 x, const Mod &md)
 {

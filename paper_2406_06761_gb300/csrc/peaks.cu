@@ -54,25 +54,34 @@ __global__ void __launch_bounds__(256) k_peak_bfly(u64 w, u64 ws, u64 *sink)
     if (acc == 0x1234567ull) sink[0] = acc;
 }
 
+// Exact multiply-accumulates in the kernels' form (28-bit limb columns):
+// CHAINS accumulators per thread, each product's first operand taken from
+// the accumulator so that nothing can be hoisted out of the loop.
 __global__ void __launch_bounds__(256) k_peak_mac(u64 b, u64 *sink)
 {
-    u64 hi[CHAINS], lo[CHAINS], a[CHAINS];
+    Acc28 acc[CHAINS];
+    u32 a0[CHAINS], a1[CHAINS], b0, b1;
+    split28(b, b0, b1);
 #pragma unroll
     for (int c = 0; c < CHAINS; c++) {
-        hi[c] = lo[c] = 0;
-        a[c] = threadIdx.x * 7919ull + c * 104729ull + blockIdx.x;
+        acc28_zero(acc[c]);
+        split28(threadIdx.x * 7919ull + c * 104729ull + blockIdx.x, a0[c], a1[c]);
     }
     for (int it = 0; it < ITERS; it++) {
 #pragma unroll
         for (int c = 0; c < CHAINS; c++) {
-            mac128(hi[c], lo[c], a[c], b);
-            a[c] += lo[c];
+            mac28(acc[c], a0[c], a1[c], b0, b1);
+            a0[c] = (u32)acc[c].c1 & 0x0FFFFFFFu;
         }
     }
-    u64 acc = 0;
+    u64 x = 0;
 #pragma unroll
-    for (int c = 0; c < CHAINS; c++) acc ^= hi[c] ^ lo[c];
-    if (acc == 0x1234567ull) sink[0] = acc;
+    for (int c = 0; c < CHAINS; c++) {
+        u64 hi, lo;
+        acc28_sum(acc[c], hi, lo);
+        x ^= hi ^ lo;
+    }
+    if (x == 0x1234567ull) sink[0] = x;
 }
 
 // 32-bit instruction streams: CHAINS independent chains per thread, the

@@ -341,19 +341,33 @@ int setup_tables(wally_ctx *c)
         const uint64_t psi = (j == c->L + 1) ? c->zeta_t : root_2n(p, c->N);
         if (!psi) return fail(WALLY_EINVAL, "no 2N-th root of unity mod %llu", (unsigned long long)p);
         NttTables t = make_tables(p, psi, c->log_n);
-        // interleaved (w, w') pairs, one 16-byte load per twiddle
-        const Tw *dptr[2];
+        // interleaved (w, w') pairs, one 16-byte load per twiddle; and the
+        // last radix-16 pass's entries 2^(S0+st) + (g << st | blk) again,
+        // k-major (k = 2^st - 1 + blk, then group g), S0 = log2 N - 4
+        const Tw *dptr[2], *lptr[2];
+        const uint32_t G = c->N / 16, S0 = c->log_n - 4;
         for (int a = 0; a < 2; a++) {
-            std::vector<uint64_t> pairs(2 * (size_t)c->N);
+            std::vector<uint64_t> pairs(2 * (size_t)c->N), last(2 * 15 * (size_t)G);
             for (uint32_t k = 0; k < c->N; k++) {
                 pairs[2 * k] = a ? t.inv[k] : t.fwd[k];
                 pairs[2 * k + 1] = a ? t.inv_s[k] : t.fwd_s[k];
             }
-            void *ptr = nullptr;
+            for (uint32_t st = 0, k = 0; st < 4; st++)
+                for (uint32_t blk = 0; blk < (1u << st); blk++, k++)
+                    for (uint32_t g = 0; g < G; g++) {
+                        const size_t src = ((size_t)1 << (S0 + st)) + (((size_t)g << st) | blk), dst = (size_t)k * G + g;
+                        last[2 * dst] = pairs[2 * src];
+                        last[2 * dst + 1] = pairs[2 * src + 1];
+                    }
+            void *ptr = nullptr, *lp = nullptr;
             CUDA_TRY(cudaMalloc(&ptr, 16 * (size_t)c->N));
             c->tables.push_back(ptr);
             CUDA_TRY(cudaMemcpy(ptr, pairs.data(), 16 * (size_t)c->N, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMalloc(&lp, 16 * 15 * (size_t)G));
+            c->tables.push_back(lp);
+            CUDA_TRY(cudaMemcpy(lp, last.data(), 16 * 15 * (size_t)G, cudaMemcpyHostToDevice));
             dptr[a] = (const Tw *)ptr;
+            lptr[a] = (const Tw *)lp;
         }
         Mod &md = dp.m[j];
         md.p = p;
@@ -367,6 +381,8 @@ int setup_tables(wally_ctx *c)
         md.n_inv_s = shoup_of(md.n_inv, p);
         md.fwd = dptr[0];
         md.inv = dptr[1];
+        md.fwd_last = lptr[0];
+        md.inv_last = lptr[1];
     }
     // CRT constants.  Delta = floor(Q/t) by long division of the product.
     const uint64_t P = c->mods[c->L], t = c->mods[c->L + 1];

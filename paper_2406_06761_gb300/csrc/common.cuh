@@ -42,6 +42,11 @@ struct Mod {
     u64 r2;            // 2^128 mod p
     u64 n_inv, n_inv_s;
     const Tw *fwd, *inv;
+    // The twiddles of the last radix-16 pass (stages log2 N - 4 .. log2 N - 1)
+    // reordered k-major: entry k * N/16 + g is the k-th twiddle of group g
+    // (k = 2^st - 1 + block for stage st), so that consecutive groups read
+    // consecutive entries.
+    const Tw *fwd_last, *inv_last;
 };
 
 // Everything a kernel needs about the parameter set (kept in device memory).

@@ -382,10 +382,14 @@ __device__ __forceinline__ void sgroup_stages(u64 *v, const Tw *tw, const Tw *tw
 }
 
 // One pass of the shared-memory core (the group and twiddle indexing of
-// common.cuh's ntt_pass); PRE: preload the group's twiddles (global table).
+// common.cuh's ntt_pass).  PRE: the last radix-16 pass (S0 = log2 N - 4,
+// one group per 16 contiguous elements), whose 15 twiddles a group are
+// preloaded from the k-major table `tws` (Mod::fwd_last / inv_last):
+// coalesced loads, a warp reading 32 consecutive entries at a time.
 template <int LOGN, int R, bool FWD, bool PRE>
 __device__ __forceinline__ void spass(u64 *sm, int S0, const Tw *tws, u64 np, u64 fp)
 {
+    static_assert(!PRE || R == 4, "the preloaded pass is the last radix-16 pass");
     constexpr int T = NttShape<LOGN>::T;
     constexpr int G = 1 << R;
     constexpr int NG = 32 / G;
@@ -400,9 +404,7 @@ __device__ __forceinline__ void spass(u64 *sm, int S0, const Tw *tws, u64 np, u6
         Tw tw[PRE ? G - 1 : 1];
         if constexpr (PRE) {
 #pragma unroll
-            for (int st = 0, k = 0; st < R; st++)
-#pragma unroll
-                for (int blk = 0; blk < (1 << st); blk++, k++) tw[k] = tws[(1 << (S0 + st)) + ((hi << st) | blk)];
+            for (int k = 0; k < G - 1; k++) tw[k] = tws[k * (1 << (LOGN - 4)) + hi];
         }
         u64 v[G];
 #pragma unroll
@@ -414,58 +416,11 @@ __device__ __forceinline__ void spass(u64 *sm, int S0, const Tw *tws, u64 np, u6
     }
 }
 
-// Forward transform of the shared-memory core with growing values: inputs
-// below B, outputs below B + 4p log2 N (the order and positions of
-// common.cuh's ntt_fwd).  Starts and ends with __syncthreads().
-template <int LOGN>
-__device__ __forceinline__ void ntt_fwd_grow(u64 *sm, Tw *cache, const Mod &md)
-{
-    using S = NttShape<LOGN>;
-    const u64 np = md.np, fp = md.four_p;
-    __syncthreads();
-    load_tw_cache<LOGN>(cache, md.fwd);
-    __syncthreads();
-    if constexpr (S::RR > 0) {
-        spass<LOGN, S::RR, true, false>(sm, 0, cache, np, fp);
-        __syncthreads();
-    }
-#pragma unroll 1
-    for (int s0 = S::RR; s0 < LOGN - 4; s0 += 4) {
-        spass<LOGN, 4, true, false>(sm, s0, cache, np, fp);
-        __syncthreads();
-    }
-    spass<LOGN, 4, true, true>(sm, LOGN - 4, md.fwd, np, fp);
-    __syncthreads();
-}
-
-// Inverse transform of the shared-memory core (values < 4p in and out, as
-// common.cuh's ntt_inv).  Starts and ends with __syncthreads().
-template <int LOGN>
-__device__ __forceinline__ void ntt_inv_keep(u64 *sm, Tw *cache, const Mod &md)
-{
-    using S = NttShape<LOGN>;
-    const u64 np = md.np, fp = md.four_p;
-    __syncthreads();
-    load_tw_cache<LOGN>(cache, md.inv);
-    spass<LOGN, 4, false, true>(sm, LOGN - 4, md.inv, np, fp);
-    __syncthreads();
-#pragma unroll 1
-    for (int s0 = LOGN - 8; s0 >= S::RR; s0 -= 4) {
-        spass<LOGN, 4, false, false>(sm, s0, cache, np, fp);
-        __syncthreads();
-    }
-    if constexpr (S::RR > 0) {
-        spass<LOGN, S::RR, false, false>(sm, 0, cache, np, fp);
-        __syncthreads();
-    }
-}
-
-// The same transforms with their first (forward) or last (inverse) memory
-// pass fused into the global load or store: the RR = log2 N mod 4 stages of
-// the remainder pass pair elements N/2 (and N/4) apart, so a thread that
-// loads an element together with its partners can run them before the
-// polynomial first reaches shared memory; and the inverse's first pass works
-// on 16 contiguous elements, which it can read straight from global memory.
+// Transforms with their remainder stages (the RR = log2 N mod 4 stages that
+// pair elements N/2 and N/4 apart) fused into the global load (forward) or
+// store (inverse): a thread that loads an element together with its
+// partners runs them before the polynomial first reaches shared memory, and
+// after it last leaves it.
 
 // Load of the input with the forward remainder stages: element e of the
 // buffer gets f(src[e], e) transformed by stages 0 .. RR-1 (values grow by
@@ -544,42 +499,24 @@ __device__ __forceinline__ void ntt_fwd_grow_rest(u64 *sm, const Tw *cache, cons
         spass<LOGN, 4, true, false>(sm, s0, cache, np, fp);
         __syncthreads();
     }
-    spass<LOGN, 4, true, true>(sm, LOGN - 4, md.fwd, np, fp);
+    spass<LOGN, 4, true, true>(sm, LOGN - 4, md.fwd_last, np, fp);
     __syncthreads();
 }
 
-// The inverse's first pass (the last radix-16 stages, groups of 16
-// contiguous elements) read from global memory (values < 4p), results into
-// the shared buffer; then the middle passes.  Loads the shared twiddle
-// cache; ends with a barrier, after which inv_store_last finishes.
+// The inverse transform up to its remainder stages, its input loaded from
+// global memory (values < 4p; coalesced, COHERENT: written earlier by this
+// kernel).  Loads the shared twiddle cache; ends with a barrier, after which
+// inv_store_last finishes.
 template <int LOGN, bool COHERENT>
 __device__ __forceinline__ void ntt_inv_keep_from(u64 *sm, Tw *cache, const u64 *src, const Mod &md)
 {
     using S = NttShape<LOGN>;
-    constexpr int T = S::T, S0 = LOGN - 4;
     const u64 np = md.np, fp = md.four_p;
-    const int tid = threadIdx.x;
     __syncthreads();  // earlier users of sm and the cache are done
     load_tw_cache<LOGN>(cache, md.inv);
-#pragma unroll 2
-    for (int u = 0; u < 2; u++) {
-        const int hi = tid + T * u, base = hi << 4;
-        Tw tw[15];
-#pragma unroll
-        for (int st = 0, k = 0; st < 4; st++)
-#pragma unroll
-            for (int blk = 0; blk < (1 << st); blk++, k++) tw[k] = md.inv[(1 << (S0 + st)) + ((hi << st) | blk)];
-        u64 v[16];
-#pragma unroll
-        for (int k = 0; k < 16; k += 2) {
-            const ulonglong2 a = COHERENT ? ld2(src + base + k) : ldg2(src + base + k);
-            v[k] = a.x;
-            v[k + 1] = a.y;
-        }
-        sgroup_stages<4, 3, false, true>(v, tw, nullptr, S0, hi, np, fp);
-#pragma unroll
-        for (int k = 0; k < 16; k++) sm[spos(base + k)] = v[k];
-    }
+    poly_load<LOGN, COHERENT>(sm, src);
+    __syncthreads();
+    spass<LOGN, 4, false, true>(sm, LOGN - 4, md.inv_last, np, fp);
     __syncthreads();
 #pragma unroll 1
     for (int s0 = LOGN - 8; s0 >= S::RR; s0 -= 4) {

@@ -202,48 +202,59 @@ __global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
     const u64 *kx = a.key + (size_t)(a.key_map ? a.key_map[x] : x) * a.key_stride;
     const u64 pol = l2_evict_first_policy();  // keys: read once a key switch
     u64 *dd = a.dd + ((size_t)x * (L + 1) + j) * L * N;
-    const int last = (j == L - 1) ? L - 2 : L - 1;  // the last digit transformed here
     for (int i = 0; i < L; i++) {
         if (i == j) continue;
         // digit i (< q_i < 2 p_j), its first stage fused into the load
         fwd_load_first<LOGN, false>(S.poly, S.twf, a.dg + ((size_t)x * L + i) * N, [](u64 v, int) { return v; }, md);
         ntt_fwd_grow_rest<LOGN>(S.poly, S.twf, md);  // lazy, < 56 p_j
-        if (i != last) {
-            u64 *di = dd + (size_t)i * N;
+        u64 *di = dd + (size_t)i * N;
 #pragma unroll 4
-            for (int u = 0; u < 16; u++) {
-                const int e = pair_elem<LOGN>(u), sp = spos(e);
-                st2(di + e, S.poly[sp], S.poly[sp ^ 1]);  // lazy
-            }
+        for (int u = 0; u < 16; u++) {
+            const int e = pair_elem<LOGN>(u), sp = spos(e);
+            st2(di + e, S.poly[sp], S.poly[sp ^ 1]);  // lazy
         }
     }
     u64 *u0 = a.u + ((size_t)x * 2 + 0) * (L + 1) * N + (size_t)j * N;
     u64 *u1 = a.u + ((size_t)x * 2 + 1) * (L + 1) * N + (size_t)j * N;
     const u64 *sc1 = a.sc + ((size_t)x * 2 * L + L + j) * N;
-#pragma unroll 2
+    // The inner product streams its operands -- per step (u, i) the thread's
+    // pair of digit i (this thread's own writes to dd, or sigma(c1) for
+    // i = j) and of the two key components -- through a ring of KS stages of
+    // cp.async copies in the shared memory the transforms used (the buffer
+    // and the twiddle cache: exactly KS stages of 3 x 16 bytes a thread).
+    // Every thread reads only its own copies, so the ring needs no barrier.
+    constexpr int T = NttShape<LOGN>::T, KS = 6, SW = 6 * T;  // SW: words a stage
+    static_assert(KS * SW == ntt_smem_words<LOGN>(), "the ring fills the transform's shared memory");
+    __syncthreads();  // every thread has stored its part of the last digit
+    u64 *ring = smraw + 2 * threadIdx.x;
+    const int steps = 16 * L;
+    int iu = 0, ii = 0, is = 0;  // the next step to copy
+    auto copy_next = [&]() {
+        if (is < steps) {
+            const int e = pair_elem<LOGN>(iu);
+            u64 *slot = ring + (size_t)(is % KS) * SW;
+            cp_async16(slot, (ii == j ? sc1 : dd + (size_t)ii * N) + e);
+            cp_async16_hint(slot + 2 * T, kx + (((size_t)ii * 2 + 0) * (L + 1) + j) * N + e, pol);
+            cp_async16_hint(slot + 4 * T, kx + (((size_t)ii * 2 + 1) * (L + 1) + j) * N + e, pol);
+            if (++ii == L) ii = 0, ++iu;
+        }
+        ++is;
+        cp_async_commit();  // one group a step, empty past the end
+    };
+    for (int k = 0; k < KS; k++) copy_next();
+    int s = 0;
     for (int u = 0; u < 16; u++) {
-        const int e = pair_elem<LOGN>(u), sp = spos(e);
+        const int e = pair_elem<LOGN>(u);
         Acc28 s0a, s0b, s1a, s1b;  // digits < 56 p_j, keys < p_j, L <= 32 terms
         acc28_zero(s0a), acc28_zero(s0b), acc28_zero(s1a), acc28_zero(s1b);
-        for (int i = 0; i < L; i++) {
-            u64 da, db;
-            if (i == j) {
-                const ulonglong2 t = ld2(sc1 + e);
-                da = t.x;
-                db = t.y;
-            } else if (i == last) {
-                da = S.poly[sp];
-                db = S.poly[sp ^ 1];
-            } else {
-                const ulonglong2 t = ld2(dd + (size_t)i * N + e);
-                da = t.x;
-                db = t.y;
-            }
-            const ulonglong2 kb = ldg2_hint(kx + (((size_t)i * 2 + 0) * (L + 1) + j) * N + e, pol);
-            const ulonglong2 ka = ldg2_hint(kx + (((size_t)i * 2 + 1) * (L + 1) + j) * N + e, pol);
+        for (int i = 0; i < L; i++, s++) {
+            cp_async_wait<KS - 1>();  // step s has landed
+            const u64 *slot = ring + (size_t)(s % KS) * SW;
+            const ulonglong2 d = ld2(slot), kb = ld2(slot + 2 * T), ka = ld2(slot + 4 * T);
+            copy_next();  // step s + KS, into the slot just read
             u32 a0, a1, b0, b1;
-            split28(da, a0, a1);
-            split28(db, b0, b1);
+            split28(d.x, a0, a1);
+            split28(d.y, b0, b1);
             mac28(s0a, a0, a1, kb.x);
             mac28(s0b, b0, b1, kb.y);
             mac28(s1a, a0, a1, ka.x);
@@ -252,6 +263,7 @@ __global__ void OLD_LB(LOGN) k_ks_b(const DevParams *dpp, RotArgs a)
         st2(u0 + e, acc28_redc(s0a, md), acc28_redc(s0b, md));
         st2(u1 + e, acc28_redc(s1a, md), acc28_redc(s1b, md));
     }
+    cp_async_wait<0>();
     if (j == L) {
         for (int c = 0; c < 2; c++) {
             u64 *uc = c ? u1 : u0;
@@ -541,11 +553,6 @@ __global__ void __launch_bounds__(256, 2) k_mac(const DevParams *dpp, ClusterSto
 // short segments (one query a cluster, as in the serving loop's waves) no
 // longer wait for their tile.  Two buffers of d_pad x ts/2 words take the
 // same shared memory as one whole tile.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
 
 template <int G>
 __global__ void __launch_bounds__(256, 2) k_mac_halves(const DevParams *dpp, ClusterStore cs, WavePlan wp,
